@@ -1,0 +1,173 @@
+/*
+ * CPU oracle for the NEON-MS sort — TEST INFRASTRUCTURE ONLY.
+ *
+ * Only the tests, the package's smoke() check and the CPU-baseline leg of the
+ * benchmark may load this library.  The product path (libnsort) never calls
+ * it and shares no code with it.
+ *
+ * What it computes is the plain definition of the result that the paper's
+ * method reaches faster: the input sequence of length N sorted ascending
+ * (paper Sec. 2.1, first paragraph), by a merge-based sort (Sec. 2.1, the
+ * merge stages; Sec. 2.4).  Here that is written as the textbook bottom-up
+ * merge sort: runs of width 1, 2, 4, ... are merged pairwise, and on equal
+ * keys the element from the left run is taken first, so the sort is stable.
+ *
+ * Keys are 32-bit patterns.  The paper sorts 32-bit integers only (Sec. 2.2);
+ * signed and IEEE binary32 keys are ordered by an order-preserving map to
+ * unsigned integers (orc_key below), which for binary32 is the IEEE 754-2008
+ * totalOrder predicate (Sec. 5.10 of that standard): -NaN < -Inf < ... < -0 <
+ * +0 < ... < +Inf < +NaN, NaNs ordered by payload.  Output keys are the input
+ * bit patterns, never canonicalised.
+ *
+ * Parity pins for every function here live in tests/test_oracle.py: brute
+ * force on tiny inputs against a textbook insertion sort, the IEEE order of a
+ * table of special values and of the signed-integer order, invariants
+ * (non-decreasing, permutation, stability) and closed forms.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+enum { ORC_U32 = 0, ORC_I32 = 1, ORC_F32 = 2 };
+
+/* Order-preserving map from a key's bit pattern to an unsigned integer.
+ * u32: identity.  i32: flip the sign bit (two's complement order).
+ * f32: negative patterns (sign set) are complemented, so that a larger
+ * magnitude maps lower; non-negative patterns get the sign bit set, so that
+ * they all map above every negative one.  Returns 0 for an unknown dtype
+ * (callers validate dtype first). */
+uint32_t orc_key(uint32_t bits, int dtype)
+{
+    if (dtype == ORC_U32)
+        return bits;
+    if (dtype == ORC_I32)
+        return bits ^ 0x80000000u;
+    if (dtype == ORC_F32) {
+        if (bits & 0x80000000u)
+            return ~bits;
+        return bits ^ 0x80000000u;
+    }
+    return 0;
+}
+
+/* Applies orc_key to n patterns (used by the tests to check the map). */
+void orc_key_array(const uint32_t *bits, uint32_t *keys, uint64_t n, int dtype)
+{
+    for (uint64_t i = 0; i < n; i++)
+        keys[i] = orc_key(bits[i], dtype);
+}
+
+/* Merges the sorted runs src[lo, mid) and src[mid, hi) into dst[lo, hi).
+ * On equal keys the left run's element goes first (stable).  vals may be
+ * NULL (keys only). */
+static void merge_runs(const uint32_t *src_k, const uint32_t *src_v,
+                       uint32_t *dst_k, uint32_t *dst_v,
+                       uint64_t lo, uint64_t mid, uint64_t hi, int dtype)
+{
+    uint64_t i = lo, j = mid, o = lo;
+    while (i < mid && j < hi) {
+        if (orc_key(src_k[j], dtype) < orc_key(src_k[i], dtype)) {
+            dst_k[o] = src_k[j];
+            if (dst_v) dst_v[o] = src_v[j];
+            j++;
+        } else {
+            dst_k[o] = src_k[i];
+            if (dst_v) dst_v[o] = src_v[i];
+            i++;
+        }
+        o++;
+    }
+    while (i < mid) {
+        dst_k[o] = src_k[i];
+        if (dst_v) dst_v[o] = src_v[i];
+        i++;
+        o++;
+    }
+    while (j < hi) {
+        dst_k[o] = src_k[j];
+        if (dst_v) dst_v[o] = src_v[j];
+        j++;
+        o++;
+    }
+}
+
+/* Stable bottom-up merge sort of n keys (and, when vals_in is not NULL, their
+ * payloads).  Output buffers may alias the inputs.  Returns 0, -1 on a bad
+ * dtype, -2 when scratch memory cannot be allocated. */
+static int sort_impl(const uint32_t *keys_in, const uint32_t *vals_in,
+                     uint32_t *keys_out, uint32_t *vals_out,
+                     uint64_t n, int dtype)
+{
+    if (dtype != ORC_U32 && dtype != ORC_I32 && dtype != ORC_F32)
+        return -1;
+    if (n == 0)
+        return 0;
+    int with_vals = (vals_in != NULL);
+    uint32_t *ak = malloc(n * sizeof(uint32_t));
+    uint32_t *bk = malloc(n * sizeof(uint32_t));
+    uint32_t *av = with_vals ? malloc(n * sizeof(uint32_t)) : NULL;
+    uint32_t *bv = with_vals ? malloc(n * sizeof(uint32_t)) : NULL;
+    if (!ak || !bk || (with_vals && (!av || !bv))) {
+        free(ak); free(bk); free(av); free(bv);
+        return -2;
+    }
+    memcpy(ak, keys_in, n * sizeof(uint32_t));
+    if (with_vals)
+        memcpy(av, vals_in, n * sizeof(uint32_t));
+
+    for (uint64_t width = 1; width < n; width *= 2) {
+        for (uint64_t lo = 0; lo < n; lo += 2 * width) {
+            uint64_t mid = lo + width < n ? lo + width : n;
+            uint64_t hi = lo + 2 * width < n ? lo + 2 * width : n;
+            merge_runs(ak, av, bk, bv, lo, mid, hi, dtype);
+        }
+        uint32_t *t = ak; ak = bk; bk = t;
+        t = av; av = bv; bv = t;
+    }
+
+    memcpy(keys_out, ak, n * sizeof(uint32_t));
+    if (with_vals)
+        memcpy(vals_out, av, n * sizeof(uint32_t));
+    free(ak); free(bk); free(av); free(bv);
+    return 0;
+}
+
+/* Keys only: out = the input bit patterns in ascending orc_key order. */
+int orc_sort_keys(const uint32_t *keys_in, uint32_t *keys_out, uint64_t n, int dtype)
+{
+    return sort_impl(keys_in, NULL, keys_out, NULL, n, dtype);
+}
+
+/* Key/value pairs, stable: equal keys keep their input order. */
+int orc_sort_pairs(const uint32_t *keys_in, const uint32_t *vals_in,
+                   uint32_t *keys_out, uint32_t *vals_out, uint64_t n, int dtype)
+{
+    if (!vals_in || !vals_out)
+        return -1;
+    return sort_impl(keys_in, vals_in, keys_out, vals_out, n, dtype);
+}
+
+/* Segmented: each [offsets[s], offsets[s+1]) is sorted on its own; segments
+ * never mix.  offsets has nseg+1 entries, offsets[0] == 0, non-decreasing.
+ * vals_in / vals_out may both be NULL (keys only).  Returns -3 on malformed
+ * offsets. */
+int orc_sort_segmented(const uint32_t *keys_in, const uint32_t *vals_in,
+                       uint32_t *keys_out, uint32_t *vals_out,
+                       const int64_t *offsets, uint64_t nseg, int dtype)
+{
+    if (offsets[0] != 0)
+        return -3;
+    for (uint64_t s = 0; s < nseg; s++)
+        if (offsets[s + 1] < offsets[s])
+            return -3;
+    if ((vals_in == NULL) != (vals_out == NULL))
+        return -1;
+    for (uint64_t s = 0; s < nseg; s++) {
+        uint64_t lo = (uint64_t)offsets[s], len = (uint64_t)(offsets[s + 1] - offsets[s]);
+        int rc = sort_impl(keys_in + lo, vals_in ? vals_in + lo : NULL,
+                           keys_out + lo, vals_out ? vals_out + lo : NULL, len, dtype);
+        if (rc != 0)
+            return rc;
+    }
+    return 0;
+}
