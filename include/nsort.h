@@ -1,0 +1,107 @@
+/*
+ * nsort — C ABI of a GB300 (sm_103a) merge sort for 32-bit keys and
+ * key/value pairs, after "A Hybrid Vectorized Merge Sort on ARM NEON"
+ * (NEON-MS, arXiv 2409.03970).
+ *
+ * The method (paper Sec. 2.1, Fig. 1-2): the input of length N is split into
+ * tiles; each tile is sorted "in registers" by a column sort with a
+ * few-comparator sorting network (Sec. 2.3, Table 1: the 60-comparator
+ * 16-input network), then merged by (hybrid) bitonic merging networks
+ * (Sec. 2.4), and the sorted tiles are merged globally with load-balanced
+ * partitioning, each worker running a serial merge of its own part
+ * (Sec. 2.1, last paragraph; Sec. 3.2 "segmentation points").
+ *
+ * Conventions shared by every entry point:
+ *  - Device pointers are plain CUDA device addresses owned by the caller
+ *    (allocated with cudaMalloc, torch, ...).  The library allocates no
+ *    device memory in nsort_keys / nsort_pairs / nsort_segmented: scratch
+ *    comes from the caller's d_tmp of at least nsort_temp_bytes() bytes.
+ *  - Keys are 32-bit patterns of type `dtype` (nsort_dtype).  They are
+ *    ordered by an order-preserving map to unsigned integers: identity for
+ *    NSORT_U32, sign-bit flip for NSORT_I32, and for NSORT_F32 the IEEE
+ *    754-2008 totalOrder (-NaN < -Inf < ... < -0 < +0 < ... < +Inf < +NaN,
+ *    NaNs by payload).  Output keys are the input bit patterns, reordered;
+ *    the map is applied inside the kernels and never visible.  Ascending.
+ *    (The paper sorts 32-bit integers only, Sec. 2.2; the signed and float
+ *    orders are this library's extension.)
+ *  - Results are unique: keys-only output is determined by the multiset of
+ *    keys; pair sorts are stable (equal keys keep input order), so the
+ *    payload order is determined too.
+ *  - in == out is allowed (in-place sort).  d_tmp must not overlap any
+ *    input or output.  Pointers need only 4-byte alignment; 16-byte aligned
+ *    buffers take the vectorised path.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t; NULL = the legacy
+ *    default stream) and return after enqueueing.  Return value: an
+ *    nsort_status.  Argument errors are detected before any launch;
+ *    NSORT_ECUDA reports a launch error (cudaGetLastError), with its text in
+ *    nsort_last_error().
+ *  - n = 0 is a valid no-op.  n up to 2^40 keys.
+ */
+#ifndef NSORT_H
+#define NSORT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { NSORT_U32 = 0, NSORT_I32 = 1, NSORT_F32 = 2 } nsort_dtype;
+
+typedef enum {
+    NSORT_KIND_KEYS = 0,            /* nsort_keys */
+    NSORT_KIND_PAIRS = 1,           /* nsort_pairs */
+    NSORT_KIND_SEGMENTED = 2,       /* nsort_segmented, keys only */
+    NSORT_KIND_SEGMENTED_PAIRS = 3  /* nsort_segmented with values */
+} nsort_kind;
+
+typedef enum {
+    NSORT_OK = 0,
+    NSORT_EINVAL = 1,     /* bad argument: dtype, kind, pointer, offsets, size */
+    NSORT_ENOMEM = 2,     /* d_tmp too small, or a request above the memory budget */
+    NSORT_ECUDA = 3,      /* a CUDA call or kernel launch failed */
+    NSORT_EBUSY = 4,      /* serving context: queue full */
+    NSORT_ETIMEOUT = 5,   /* nsort_wait deadline passed */
+    NSORT_ENOTFOUND = 6   /* serving context: unknown ticket */
+} nsort_status;
+
+/* Scratch bytes a call of `kind` needs for n keys (and nseg segments, for
+ * the segmented kinds; ignored otherwise).  dtype does not change the size.
+ * Returns 0 for a bad kind.  Source: the auxiliary O(N) buffer of the
+ * paper's merge stages (Sec. 3.2, last paragraph): one ping-pong copy of the
+ * keys (and values), plus the per-tile merge-path splitters. */
+size_t nsort_temp_bytes(int kind, uint64_t n, uint64_t nseg, int dtype);
+
+/* Number of passes over the data for a plain sort of n keys (kind KEYS or
+ * PAIRS): one tile sort plus ceil(log2(ceil(n / tile))) global merge passes.
+ * Writes the tile sizes through the non-NULL pointers.  Used to compute the
+ * algorithmic bytes of a sort (passes x 2 x element bytes x n). */
+int nsort_plan(int kind, uint64_t n, int *passes, int *sort_tile, int *merge_tile);
+
+/* Sorts n keys ascending (paper Sec. 2.1: "the input sequence of the length
+ * N").  d_keys_in / d_keys_out: n 32-bit patterns, contiguous.  d_tmp:
+ * nsort_temp_bytes(NSORT_KIND_KEYS, n, 0, dtype) bytes of device scratch,
+ * 256-byte aligned.  Errors: NSORT_EINVAL (NULL pointer with n > 0, bad
+ * dtype, n too large), NSORT_ENOMEM (tmp_bytes too small), NSORT_ECUDA. */
+int nsort_keys(const void *d_keys_in, void *d_keys_out, uint64_t n, int dtype,
+               void *d_tmp, size_t tmp_bytes, void *stream);
+
+/* Stable key/value sort: keys as in nsort_keys, each carrying a 32-bit
+ * payload (separate arrays, same length).  Equal keys keep their input
+ * order.  d_vals_in == d_vals_out is allowed.  Scratch:
+ * nsort_temp_bytes(NSORT_KIND_PAIRS, n, 0, dtype).  Errors as nsort_keys. */
+int nsort_pairs(const void *d_keys_in, const uint32_t *d_vals_in,
+                void *d_keys_out, uint32_t *d_vals_out, uint64_t n, int dtype,
+                void *d_tmp, size_t tmp_bytes, void *stream);
+
+/* Human-readable text of an nsort_status. */
+const char *nsort_status_string(int status);
+/* Text of the last NSORT_ECUDA error on the calling host thread ("" if none). */
+const char *nsort_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NSORT_H */

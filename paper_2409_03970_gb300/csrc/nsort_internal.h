@@ -1,0 +1,42 @@
+// Host-side helpers shared by the translation units of libnsort.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+namespace nsort {
+
+// Largest key count a call accepts (keeps every in-kernel index in range).
+constexpr uint64_t MAX_KEYS = uint64_t(1) << 40;
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Layout of the scratch buffer of a plain sort.
+struct Plan {
+  int64_t n = 0;
+  int sort_tile = 0;         // keys per tile-sort CTA
+  int merge_tile = 0;        // outputs per merge CTA
+  int merge_passes = 0;      // ceil(log2(ceil(n / sort_tile)))
+  int64_t num_merge_tiles = 0;
+  size_t keys_off = 0;       // ping-pong key buffer
+  size_t vals_off = 0;       // ping-pong value buffer (pairs)
+  size_t split_off = 0;      // num_merge_tiles + 1 int64 splitters
+  size_t total = 0;          // bytes of scratch (0 when one tile holds everything)
+};
+
+Plan make_plan(int kind, uint64_t n);
+
+int sort_keys_impl(const uint32_t *in, uint32_t *out, int64_t n, int dt, void *tmp,
+                   cudaStream_t st);
+int sort_pairs_impl(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
+                    int64_t n, int dt, void *tmp, cudaStream_t st);
+
+size_t segmented_temp_bytes(int kind, uint64_t n, uint64_t nseg);
+
+void set_last_error(const std::string &msg);
+const char *last_error_cstr();
+
+}  // namespace nsort

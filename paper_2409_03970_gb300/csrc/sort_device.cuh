@@ -1,0 +1,206 @@
+// Device building blocks of the NEON-MS sort on sm_103a.
+//
+// The paper's three merge levels (Sec. 2.1, Fig. 1) become thread / warp /
+// block / grid levels here:
+//   column sort   (Sec. 2.3)  16 keys in one thread's registers, sorted by the
+//                             60-comparator 16-input network;
+//   row merge     (Sec. 2.4)  the 32 sorted 16-runs of a warp are merged by
+//                             flip ("asymmetric") bitonic merging networks:
+//                             stages whose comparators span lanes use warp
+//                             shuffles (the vectorised part), the last four
+//                             stages run inside each thread (the serial tail
+//                             of the hybrid merger);
+//   vectorised / parallel merge (Sec. 2.1, last paragraph) merge path: each
+//                             thread finds its share of a merge by a binary
+//                             search on the cross diagonal and runs a
+//                             branch-free serial merge of it.
+// Keys travel as unsigned integers after an order-preserving map (to_key);
+// pair sorts use 64-bit composites (key << 32 | position) in the networks,
+// which makes every composite distinct and the result stable.
+#pragma once
+
+#include <cstdint>
+
+namespace nsort {
+
+enum { DT_U32 = 0, DT_I32 = 1, DT_F32 = 2 };
+
+// Order-preserving map of a 32-bit pattern to an unsigned key.
+//  u32: identity.  i32: flip the sign bit.  f32: negatives (sign set) are
+//  complemented, non-negatives get the sign bit set — IEEE totalOrder.
+__device__ __forceinline__ uint32_t to_key(uint32_t b, int dt) {
+  uint32_t m = 0u;
+  if (dt == DT_I32) m = 0x80000000u;
+  if (dt == DT_F32) m = (uint32_t)((int32_t)b >> 31) | 0x80000000u;
+  return b ^ m;
+}
+
+// Inverse of to_key.
+__device__ __forceinline__ uint32_t from_key(uint32_t k, int dt) {
+  uint32_t m = 0u;
+  if (dt == DT_I32) m = 0x80000000u;
+  if (dt == DT_F32) m = (uint32_t)((int32_t)~k >> 31) | 0x80000000u;
+  return k ^ m;
+}
+
+// Shared-memory index with one pad word per 32 (u32) or per 16 (u64)
+// elements: a thread writing 16 consecutive elements and a warp reading
+// consecutive elements are both free of bank conflicts.
+template <typename K> struct Pad;
+template <> struct Pad<uint32_t> { static constexpr int SHIFT = 5; };
+template <> struct Pad<uint64_t> { static constexpr int SHIFT = 4; };
+template <typename K>
+__device__ __forceinline__ int pidx(int e) { return e + (e >> Pad<K>::SHIFT); }
+template <typename K>
+__host__ __device__ constexpr int padded_len(int tile) { return tile + (tile >> Pad<K>::SHIFT) + 2; }
+
+// ---- compare-exchange --------------------------------------------------
+__device__ __forceinline__ uint32_t kmin(uint32_t a, uint32_t b) { return a < b ? a : b; }
+__device__ __forceinline__ uint32_t kmax(uint32_t a, uint32_t b) { return a < b ? b : a; }
+__device__ __forceinline__ uint64_t kmin(uint64_t a, uint64_t b) { return a < b ? a : b; }
+__device__ __forceinline__ uint64_t kmax(uint64_t a, uint64_t b) { return a < b ? b : a; }
+
+template <typename K>
+__device__ __forceinline__ void ce(K &a, K &b) {
+  const K lo = kmin(a, b);
+  b = kmax(a, b);
+  a = lo;
+}
+
+// ---- column sort: the 16-input network (Sec. 2.3, Table 1) --------------
+// M. W. Green's network, 60 comparators in 10 layers: four layers compare
+// the wires whose indices differ in one bit (a 4-cube), six more finish.
+template <typename K>
+__device__ __forceinline__ void column_sort16(K (&r)[16]) {
+#pragma unroll
+  for (int bit = 1; bit < 16; bit <<= 1) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      if (!(i & bit)) ce(r[i], r[i | bit]);
+  }
+  ce(r[5], r[10]); ce(r[6], r[9]); ce(r[3], r[12]); ce(r[13], r[14]);
+  ce(r[7], r[11]); ce(r[1], r[2]); ce(r[4], r[8]);
+  ce(r[1], r[4]); ce(r[7], r[13]); ce(r[2], r[8]); ce(r[11], r[14]);
+  ce(r[5], r[6]); ce(r[9], r[10]);
+  ce(r[2], r[4]); ce(r[11], r[13]); ce(r[3], r[8]); ce(r[7], r[12]);
+  ce(r[6], r[8]); ce(r[10], r[12]); ce(r[3], r[5]); ce(r[7], r[9]);
+  ce(r[3], r[4]); ce(r[5], r[6]); ce(r[7], r[8]); ce(r[9], r[10]); ce(r[11], r[12]);
+  ce(r[6], r[7]); ce(r[8], r[9]);
+}
+
+// ---- warp-level flip merging network (Sec. 2.4) -------------------------
+__device__ __forceinline__ uint32_t shfl_x(uint32_t v, int m) {
+  return __shfl_xor_sync(0xffffffffu, v, m);
+}
+__device__ __forceinline__ uint64_t shfl_x(uint64_t v, int m) {
+  const uint32_t lo = __shfl_xor_sync(0xffffffffu, (uint32_t)v, m);
+  const uint32_t hi = __shfl_xor_sync(0xffffffffu, (uint32_t)(v >> 32), m);
+  return ((uint64_t)hi << 32) | lo;
+}
+template <typename K>
+__device__ __forceinline__ K keep(bool lower, K mine, K other) {
+  return lower ? kmin(mine, other) : kmax(mine, other);
+}
+
+// In-thread half-cleaners at distances 8, 4, 2, 1: sorts each thread's 16
+// registers once they form a bitonic sequence (the serial tail).
+template <typename K>
+__device__ __forceinline__ void thread_tail16(K (&r)[16]) {
+#pragma unroll
+  for (int d = 8; d >= 1; d >>= 1) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      if (!(i & d)) ce(r[i], r[i + d]);
+  }
+}
+
+// Lane l holds a sorted run of 16 in r[0..15] (warp element 16*l + k).
+// Merges the 32 runs into one sorted run of 512 in five levels.  Level j
+// merges groups of 2^(j-1) lanes pairwise: a flip stage (element p against
+// element 2m-1-p of the 2m-element group: lane l ^ (2^j - 1), register
+// 15 - k), half-cleaner stages across lanes at lane distances 2^(j-2)..1,
+// then the in-thread tail.  In each cross-lane comparator the lower lane
+// keeps the minimum and the upper lane the maximum.
+template <typename K>
+__device__ __forceinline__ void warp_merge512(K (&r)[16], int lane) {
+#pragma unroll
+  for (int j = 1; j <= 5; ++j) {
+    const int span = 1 << j;
+    const bool lower = !(lane & (span >> 1));
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const K from_hi = shfl_x(r[15 - k], span - 1);   // partner's mirror of r[k]
+      const K from_lo = shfl_x(r[k], span - 1);        // partner's mirror of r[15-k]
+      r[k] = keep(lower, r[k], from_hi);
+      r[15 - k] = keep(lower, r[15 - k], from_lo);
+    }
+#pragma unroll
+    for (int d = span >> 2; d >= 1; d >>= 1) {
+      const bool lo2 = !(lane & d);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) r[k] = keep(lo2, r[k], shfl_x(r[k], d));
+    }
+    thread_tail16(r);
+  }
+}
+
+// ---- merge path (Sec. 2.1: load-balanced partitioning) -------------------
+// Number of elements of A among the first `diag` outputs of the stable
+// merge of A[0, na) and B[0, nb) (A wins ties).  Shared-memory runs at
+// element offsets a0 / b0 in the padded layout.
+template <typename K>
+__device__ __forceinline__ int merge_path_smem(const K *s, int a0, int na, int b0, int nb,
+                                               int diag) {
+  int lo = diag - nb > 0 ? diag - nb : 0;
+  int hi = diag < na ? diag : na;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (s[pidx<K>(a0 + mid)] <= s[pidx<K>(b0 + diag - 1 - mid)]) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Same search on global memory (64-bit lengths).
+__device__ __forceinline__ int64_t merge_path_global(const uint32_t *A, int64_t na,
+                                                     const uint32_t *B, int64_t nb,
+                                                     int64_t diag) {
+  int64_t lo = diag - nb > 0 ? diag - nb : 0;
+  int64_t hi = diag < na ? diag : na;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (A[mid] <= B[diag - 1 - mid]) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// ---- serial merge (the serial half of the hybrid merger) ----------------
+// Produces VT outputs of the stable merge of s[a, a_end) and s[b, b_end)
+// (element indices, padded layout) into out[].  Branch-free: one compare,
+// selects and one shared load per output.  Indices are clamped to `limit`
+// (the last readable element) so that a thread whose range runs past the
+// end of both runs never reads outside the buffer; such outputs are
+// discarded by the caller.  src[k] receives the element index each output
+// came from when TRACK is set.
+template <int VT, bool TRACK, typename K>
+__device__ __forceinline__ void serial_merge(const K *s, int a, int a_end, int b, int b_end,
+                                             int limit, K (&out)[VT], int (&src)[VT]) {
+  K ka = s[pidx<K>(a < limit ? a : limit)];
+  K kb = s[pidx<K>(b < limit ? b : limit)];
+#pragma unroll
+  for (int k = 0; k < VT; ++k) {
+    const bool take_a = (b >= b_end) || (a < a_end && ka <= kb);
+    out[k] = take_a ? ka : kb;
+    if (TRACK) src[k] = take_a ? a : b;
+    int nxt = (take_a ? a : b) + 1;
+    nxt = nxt < limit ? nxt : limit;
+    const K kn = s[pidx<K>(nxt)];
+    ka = take_a ? kn : ka;
+    kb = take_a ? kb : kn;
+    a += take_a;
+    b += !take_a;
+  }
+}
+
+}  // namespace nsort

@@ -1,0 +1,177 @@
+"""Thin ctypes binding of libnsort (include/nsort.h): the same entry points,
+with argument marshalling only.  Every step of a sort runs in the CUDA
+kernels of libnsort; torch only provides device memory and streams.
+
+The raw names (``nsort_keys``, ``nsort_pairs``, ...) take torch tensors or
+integer device addresses.  ``sort`` / ``sort_pairs`` are conveniences that
+allocate the output and the scratch with torch and raise on error.
+
+There is no CPU fallback: if libnsort.so has not been built this module
+raises on first use.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libnsort.so")
+
+U32, I32, F32 = 0, 1, 2
+KIND_KEYS, KIND_PAIRS, KIND_SEGMENTED, KIND_SEGMENTED_PAIRS = 0, 1, 2, 3
+OK, EINVAL, ENOMEM, ECUDA, EBUSY, ETIMEOUT, ENOTFOUND = range(7)
+
+_lock = threading.Lock()
+_lib = None
+
+
+class NsortError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        lib = _load()
+        msg = lib.nsort_status_string(status).decode()
+        detail = lib.nsort_last_error().decode()
+        super().__init__(f"{what}: {msg} ({status}){': ' + detail if detail else ''}")
+        self.status = status
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"libnsort.so is not built ({LIB_PATH}); run "
+                "`python -c 'import __graft_entry__ as g; g.build()'` first")
+        lib = ctypes.CDLL(LIB_PATH)
+        vp, u64, i32, sz = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_size_t
+        ip = ctypes.POINTER(ctypes.c_int)
+        lib.nsort_temp_bytes.argtypes = [i32, u64, u64, i32]
+        lib.nsort_temp_bytes.restype = sz
+        lib.nsort_plan.argtypes = [i32, u64, ip, ip, ip]
+        lib.nsort_plan.restype = i32
+        lib.nsort_keys.argtypes = [vp, vp, u64, i32, vp, sz, vp]
+        lib.nsort_keys.restype = i32
+        lib.nsort_pairs.argtypes = [vp, vp, vp, vp, u64, i32, vp, sz, vp]
+        lib.nsort_pairs.restype = i32
+        lib.nsort_status_string.argtypes = [i32]
+        lib.nsort_status_string.restype = ctypes.c_char_p
+        lib.nsort_last_error.argtypes = []
+        lib.nsort_last_error.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+def lib():
+    """The loaded ctypes library (loads it on first call)."""
+    return _load()
+
+
+# ---- marshalling ------------------------------------------------------------
+
+def _ptr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def dtype_code(t) -> int:
+    """nsort_dtype of a torch tensor (uint32 / int32 / float32)."""
+    import torch
+    codes = {torch.int32: I32, torch.float32: F32}
+    if hasattr(torch, "uint32"):
+        codes[torch.uint32] = U32
+    if t.dtype not in codes:
+        raise TypeError(f"keys must be uint32, int32 or float32, not {t.dtype}")
+    return codes[t.dtype]
+
+
+def _check_1d(t, name):
+    if not t.is_cuda or not t.is_contiguous() or t.dim() != 1:
+        raise ValueError(f"{name} must be a contiguous 1-D CUDA tensor")
+
+
+# ---- raw entry points (same names as the C ABI) ----------------------------
+
+def nsort_temp_bytes(kind: int, n: int, nseg: int = 0, dtype: int = U32) -> int:
+    return int(_load().nsort_temp_bytes(kind, n, nseg, dtype))
+
+
+def nsort_plan(kind: int, n: int):
+    """(passes, sort_tile, merge_tile) of a plain sort of n keys."""
+    p, s, m = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    rc = _load().nsort_plan(kind, n, ctypes.byref(p), ctypes.byref(s), ctypes.byref(m))
+    if rc != OK:
+        raise NsortError(rc, "nsort_plan")
+    return p.value, s.value, m.value
+
+
+def nsort_keys(keys_in, keys_out, n: int, dtype: int, tmp, tmp_bytes: int, stream=None) -> int:
+    return _load().nsort_keys(_ptr(keys_in), _ptr(keys_out), n, dtype, _ptr(tmp), tmp_bytes,
+                              _stream(stream))
+
+
+def nsort_pairs(keys_in, vals_in, keys_out, vals_out, n: int, dtype: int, tmp, tmp_bytes: int,
+                stream=None) -> int:
+    return _load().nsort_pairs(_ptr(keys_in), _ptr(vals_in), _ptr(keys_out), _ptr(vals_out), n,
+                               dtype, _ptr(tmp), tmp_bytes, _stream(stream))
+
+
+# ---- conveniences -----------------------------------------------------------
+
+def scratch(kind: int, n: int, nseg: int = 0, device=None):
+    """A uint8 device tensor of nsort_temp_bytes(kind, n, nseg) bytes (at
+    least one byte, so that it has an address)."""
+    import torch
+    nbytes = max(1, nsort_temp_bytes(kind, n, nseg))
+    return torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
+
+
+def sort(keys, out=None, tmp=None, stream=None):
+    """Sorts a 1-D CUDA tensor of uint32 / int32 / float32 keys ascending
+    (float32 in IEEE totalOrder).  Returns `out` (new tensor if None)."""
+    import torch
+    _check_1d(keys, "keys")
+    dt = dtype_code(keys)
+    n = keys.numel()
+    if out is None:
+        out = torch.empty_like(keys)
+    _check_1d(out, "out")
+    if tmp is None:
+        tmp = scratch(KIND_KEYS, n, device=keys.device)
+    rc = nsort_keys(keys, out, n, dt, tmp, tmp.numel(), stream)
+    if rc != OK:
+        raise NsortError(rc, "nsort_keys")
+    return out
+
+
+def sort_pairs(keys, vals, keys_out=None, vals_out=None, tmp=None, stream=None):
+    """Stable sort of (key, uint32/int32 payload) pairs by key.  Returns
+    (keys_out, vals_out)."""
+    import torch
+    _check_1d(keys, "keys")
+    _check_1d(vals, "vals")
+    if vals.numel() != keys.numel() or vals.element_size() != 4:
+        raise ValueError("vals must be a 32-bit tensor of the same length as keys")
+    dt = dtype_code(keys)
+    n = keys.numel()
+    keys_out = torch.empty_like(keys) if keys_out is None else keys_out
+    vals_out = torch.empty_like(vals) if vals_out is None else vals_out
+    if tmp is None:
+        tmp = scratch(KIND_PAIRS, n, device=keys.device)
+    rc = nsort_pairs(keys, vals, keys_out, vals_out, n, dt, tmp, tmp.numel(), stream)
+    if rc != OK:
+        raise NsortError(rc, "nsort_pairs")
+    return keys_out, vals_out

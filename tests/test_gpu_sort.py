@@ -1,0 +1,192 @@
+"""GPU parity: libnsort (through the C ABI) against the CPU oracle, bit for
+bit, on seeded inputs.  Sizes span one to many tiles with ragged tails;
+every dtype and input distribution; in-place and misaligned buffers; the
+full-size benchmark workloads (2^28 keys, 2^27 pairs)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2409_03970_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DT = {"u32": 0, "i32": 1, "f32": 2}
+
+
+@pytest.fixture(scope="module")
+def ns():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2409_03970_gb300 import build, nsort
+    build.build()
+    nsort.lib()
+    return nsort
+
+
+def dev(bits):
+    return torch.from_numpy(np.ascontiguousarray(bits).view(np.int32)).cuda()
+
+
+def host(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+def gpu_sort(ns, bits, dt, inplace=False, offset=0):
+    n = bits.size
+    x = dev(np.concatenate([np.zeros(offset, np.uint32), bits]))[offset:]
+    out = x if inplace else torch.empty(n + offset, dtype=torch.int32, device="cuda")[offset:]
+    tmp = ns.scratch(ns.KIND_KEYS, n)
+    rc = ns.nsort_keys(x, out, n, DT[dt], tmp, tmp.numel())
+    assert rc == ns.OK, ns.lib().nsort_last_error()
+    return host(out)
+
+
+def gpu_pairs(ns, k, v, dt, inplace=False):
+    n = k.size
+    kt, vt = dev(k), dev(v)
+    ko, vo = (kt, vt) if inplace else (torch.empty_like(kt), torch.empty_like(vt))
+    tmp = ns.scratch(ns.KIND_PAIRS, n)
+    rc = ns.nsort_pairs(kt, vt, ko, vo, n, DT[dt], tmp, tmp.numel())
+    assert rc == ns.OK, ns.lib().nsort_last_error()
+    return host(ko), host(vo)
+
+
+SIZES = [0, 1, 2, 3, 15, 16, 17, 511, 512, 513, 4095, 4096, 4097, 8191, 8192, 8193,
+         3 * 8192 + 5, 65536 + 1, 100_003, 1 << 20, (1 << 20) + 12345]
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_keys_u32_uniform_sizes(ns, n):
+    x = inputs.keys(n, "u32", "uniform", seed=n)
+    np.testing.assert_array_equal(gpu_sort(ns, x, "u32"), oracle.sort_keys(x, "u32"))
+
+
+@pytest.mark.parametrize("dt", ["u32", "i32", "f32"])
+@pytest.mark.parametrize("dist", list(inputs.DISTRIBUTIONS))
+@pytest.mark.parametrize("n", [8193, 250_001, (1 << 21) + 3])
+def test_keys_all_dtypes_distributions(ns, dt, dist, n):
+    x = inputs.keys(n, dt, dist, seed=1)
+    np.testing.assert_array_equal(gpu_sort(ns, x, dt), oracle.sort_keys(x, dt))
+
+
+def test_keys_f32_specials_and_nan_payloads(ns):
+    k, _ = inputs.normal_pairs(300_000, seed=2, special_per_mille=100)
+    extra = np.array([0xFFFFFFFF, 0xFFC00001, 0xFF800001, 0x7F800001, 0x7FBFFFFF,
+                      0x7FFFFFFF, 0x00000001, 0x80000001, 0x007FFFFF, 0x807FFFFF], np.uint32)
+    k = np.concatenate([k, np.repeat(extra, 100)])
+    np.testing.assert_array_equal(gpu_sort(ns, k, "f32"), oracle.sort_keys(k, "f32"))
+
+
+@pytest.mark.parametrize("n", [5, 8192, 40_000, 1 << 20])
+def test_keys_in_place(ns, n):
+    x = inputs.keys(n, "i32", "zipf", seed=3)
+    np.testing.assert_array_equal(gpu_sort(ns, x, "i32", inplace=True), oracle.sort_keys(x, "i32"))
+
+
+@pytest.mark.parametrize("offset", [1, 2, 3])
+def test_keys_misaligned_buffers(ns, offset):
+    x = inputs.keys(70_001, "u32", "uniform", seed=offset)
+    np.testing.assert_array_equal(gpu_sort(ns, x, "u32", offset=offset), oracle.sort_keys(x, "u32"))
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 17, 4095, 4096, 4097, 12289, 100_000, 1 << 20, (1 << 20) + 7])
+def test_pairs_normal_with_specials(ns, n):
+    k, v = inputs.normal_pairs(n, seed=n, special_per_mille=5)
+    ko, vo = gpu_pairs(ns, k, v, "f32")
+    wk, wv = oracle.sort_pairs(k, v, "f32")
+    np.testing.assert_array_equal(ko, wk)
+    np.testing.assert_array_equal(vo, wv)
+
+
+@pytest.mark.parametrize("dt", ["u32", "i32", "f32"])
+@pytest.mark.parametrize("dist", ["dup16", "zipf", "sorted", "reverse"])
+def test_pairs_stability_heavy_duplicates(ns, dt, dist):
+    n = 300_007
+    k = inputs.keys(n, dt, dist, seed=4)
+    v = inputs.counter_u32(4, 6, 0, n)            # arbitrary payloads, not the index
+    ko, vo = gpu_pairs(ns, k, v, dt)
+    wk, wv = oracle.sort_pairs(k, v, dt)
+    np.testing.assert_array_equal(ko, wk)
+    np.testing.assert_array_equal(vo, wv)
+
+
+def test_pairs_in_place(ns):
+    k = inputs.keys(50_000, "u32", "dup16", seed=5)
+    v = np.arange(k.size, dtype=np.uint32)
+    ko, vo = gpu_pairs(ns, k, v, "u32", inplace=True)
+    wk, wv = oracle.sort_pairs(k, v, "u32")
+    np.testing.assert_array_equal(ko, wk)
+    np.testing.assert_array_equal(vo, wv)
+
+
+def test_scratch_too_small_is_rejected(ns):
+    n = 1 << 16
+    x = dev(inputs.keys(n, "u32", "uniform", seed=0))
+    tmp = ns.scratch(ns.KIND_KEYS, n)
+    assert ns.nsort_keys(x, x, n, 0, tmp, tmp.numel() - 1) == ns.ENOMEM
+
+
+# ---- full-size benchmark workloads -----------------------------------------
+
+def test_full_size_u32_uniform_against_oracle(ns):
+    """The benchmark workload, 2^28 uniform uint32 keys, seed 0, in the
+    launch configuration the benchmark times, compared element by element."""
+    n = 1 << 28
+    x = inputs.keys(n, "u32", "uniform", seed=0)
+    got = gpu_sort(ns, x, "u32")
+    want = oracle.sort_keys(x, "u32")
+    assert np.array_equal(got, want)
+
+
+def _key_i64(t, dt):
+    """Order key of int32 tensor patterns, as non-negative int64 (test-side)."""
+    if dt == "u32":
+        return t.to(torch.int64) & 0xFFFFFFFF
+    if dt == "i32":
+        return t.to(torch.int64) + (1 << 31)
+    m = (t >> 31) | torch.tensor(-(1 << 31), dtype=torch.int32, device=t.device)
+    return (t ^ m).to(torch.int64) & 0xFFFFFFFF
+
+
+@pytest.mark.parametrize("dt", ["i32", "f32"])
+@pytest.mark.parametrize("dist", list(inputs.DISTRIBUTIONS))
+def test_full_size_properties(ns, dt, dist):
+    """2^28 keys of each dtype and distribution: the output is non-decreasing
+    in key order; it is a permutation of the input (a 2^16-bucket histogram
+    of the keys and a 64-bit multiset hash agree); and sampled output
+    positions hold the right order statistics (for out[i] = v: fewer than
+    i+1 input keys are below v and more than i are at most v)."""
+    n = 1 << 28
+    x = inputs.keys(n, dt, dist, seed=2)
+    xt = dev(x)
+    del x
+    out = torch.empty_like(xt)
+    tmp = ns.scratch(ns.KIND_KEYS, n)
+    assert ns.nsort_keys(xt, out, n, DT[dt], tmp, tmp.numel()) == ns.OK
+    del tmp
+    k = _key_i64(out, dt)
+    assert bool((k[1:] >= k[:-1]).all())
+    ki = _key_i64(xt, dt)
+    h_in = torch.bincount((ki >> 16), minlength=1 << 16)
+    h_out = torch.bincount((k >> 16), minlength=1 << 16)
+    assert torch.equal(h_in, h_out)
+    c1, c2 = 0x9E3779B97F4A7C15 - (1 << 64), 0xBF58476D1CE4E5B9 - (1 << 64)
+    mix = lambda z: ((z * c1) ^ (z >> 29)) * c2          # int64, wraps mod 2^64
+    assert int(mix(ki).sum()) == int(mix(k).sum())
+    # patterns, not just keys: the key map is a bijection, so equal keys are equal patterns
+    assert int(xt.to(torch.int64).sum()) == int(out.to(torch.int64).sum())
+    for i in inputs.counter_u64(9, 0, 0, 12) % np.uint64(n):
+        i = int(i)
+        v = k[i]
+        assert int((ki < v).sum()) <= i < int((ki <= v).sum())
+
+
+def test_full_size_pairs_against_oracle(ns):
+    """2^27 float32 Normal(0,1) keys with 0.1% IEEE specials, payload = index."""
+    n = 1 << 27
+    k, v = inputs.normal_pairs(n, seed=0)
+    ko, vo = gpu_pairs(ns, k, v, "f32")
+    wk, wv = oracle.sort_pairs(k, v, "f32")
+    assert np.array_equal(ko, wk)
+    assert np.array_equal(vo, wv)
