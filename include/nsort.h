@@ -95,6 +95,23 @@ int nsort_pairs(const void *d_keys_in, const uint32_t *d_vals_in,
                 void *d_keys_out, uint32_t *d_vals_out, uint64_t n, int dtype,
                 void *d_tmp, size_t tmp_bytes, void *stream);
 
+/* ---- tracing ------------------------------------------------------------
+ * Per-kernel device time without a profiler.  While enabled, every kernel
+ * launch of the library is bracketed by CUDA events recorded on the stream
+ * it is launched on.  Do not enable while a stream is being captured into a
+ * CUDA graph.  Paper: none (measurement support). */
+typedef struct {
+    char kernel[32];     /* kernel name, e.g. "merge_keys" */
+    uint64_t launches;   /* launches recorded since tracing was enabled */
+    double total_ms;     /* sum of their device durations */
+} nsort_trace_entry;
+
+/* on != 0 starts recording (dropping earlier records); on == 0 stops. */
+int nsort_trace_enable(int on);
+/* Waits for the recorded events, writes one entry per kernel name (at most
+ * `capacity`; *count = number of names seen) and drops the records. */
+int nsort_trace_read(nsort_trace_entry *out, int capacity, int *count);
+
 /* Human-readable text of an nsort_status. */
 const char *nsort_status_string(int status);
 /* Text of the last NSORT_ECUDA error on the calling host thread ("" if none). */

@@ -366,16 +366,25 @@ int sort_keys_impl(const uint32_t *in, uint32_t *out, int64_t n, int dt, void *t
                        : nullptr;
   int cur = p.merge_passes % 2;  // the last pass must land in bufs[0] == out
   const int64_t tiles = (n + p.sort_tile - 1) / p.sort_tile;
-  tile_sort_keys_kernel<KEYS_SORT_NT><<<(unsigned)tiles, KEYS_SORT_NT, 0, st>>>(
-      in, bufs[cur], n, dt, p.merge_passes == 0 ? dt : DT_U32);
+  {
+    TraceScope tr(TK_TILE_SORT_KEYS, st);
+    tile_sort_keys_kernel<KEYS_SORT_NT><<<(unsigned)tiles, KEYS_SORT_NT, 0, st>>>(
+        in, bufs[cur], n, dt, p.merge_passes == 0 ? dt : DT_U32);
+  }
   int rc = launch_status("tile_sort_keys");
   for (int pass = 0; rc == NSORT_OK && pass < p.merge_passes; ++pass) {
     const int64_t run = (int64_t)p.sort_tile << pass;
     const unsigned pblocks = (unsigned)((p.num_merge_tiles + 255) / 256);
-    partition_kernel<<<pblocks, 256, 0, st>>>(bufs[cur], n, run, p.merge_tile,
-                                              p.num_merge_tiles, split);
-    merge_keys_kernel<MERGE_NT, MERGE_VT><<<(unsigned)p.num_merge_tiles, MERGE_NT, 0, st>>>(
-        bufs[cur], bufs[cur ^ 1], n, run, split, pass == p.merge_passes - 1 ? dt : DT_U32);
+    {
+      TraceScope tr(TK_PARTITION, st);
+      partition_kernel<<<pblocks, 256, 0, st>>>(bufs[cur], n, run, p.merge_tile,
+                                                p.num_merge_tiles, split);
+    }
+    {
+      TraceScope tr(TK_MERGE_KEYS, st);
+      merge_keys_kernel<MERGE_NT, MERGE_VT><<<(unsigned)p.num_merge_tiles, MERGE_NT, 0, st>>>(
+          bufs[cur], bufs[cur ^ 1], n, run, split, pass == p.merge_passes - 1 ? dt : DT_U32);
+    }
     rc = launch_status("merge_keys");
     cur ^= 1;
   }
@@ -393,17 +402,26 @@ int sort_pairs_impl(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, ui
   int64_t *split = p.merge_passes ? reinterpret_cast<int64_t *>(t + p.split_off) : nullptr;
   int cur = p.merge_passes % 2;
   const int64_t tiles = (n + p.sort_tile - 1) / p.sort_tile;
-  tile_sort_pairs_kernel<PAIRS_SORT_NT><<<(unsigned)tiles, PAIRS_SORT_NT, PAIRS_SORT_SMEM, st>>>(
-      kin, vin, kb[cur], vb[cur], n, dt, p.merge_passes == 0 ? dt : DT_U32);
+  {
+    TraceScope tr(TK_TILE_SORT_PAIRS, st);
+    tile_sort_pairs_kernel<PAIRS_SORT_NT><<<(unsigned)tiles, PAIRS_SORT_NT, PAIRS_SORT_SMEM, st>>>(
+        kin, vin, kb[cur], vb[cur], n, dt, p.merge_passes == 0 ? dt : DT_U32);
+  }
   rc = launch_status("tile_sort_pairs");
   for (int pass = 0; rc == NSORT_OK && pass < p.merge_passes; ++pass) {
     const int64_t run = (int64_t)p.sort_tile << pass;
     const unsigned pblocks = (unsigned)((p.num_merge_tiles + 255) / 256);
-    partition_kernel<<<pblocks, 256, 0, st>>>(kb[cur], n, run, p.merge_tile,
-                                              p.num_merge_tiles, split);
-    merge_pairs_kernel<PMERGE_NT, PMERGE_VT><<<(unsigned)p.num_merge_tiles, PMERGE_NT, 0, st>>>(
-        kb[cur], vb[cur], kb[cur ^ 1], vb[cur ^ 1], n, run, split,
-        pass == p.merge_passes - 1 ? dt : DT_U32);
+    {
+      TraceScope tr(TK_PARTITION, st);
+      partition_kernel<<<pblocks, 256, 0, st>>>(kb[cur], n, run, p.merge_tile,
+                                                p.num_merge_tiles, split);
+    }
+    {
+      TraceScope tr(TK_MERGE_PAIRS, st);
+      merge_pairs_kernel<PMERGE_NT, PMERGE_VT><<<(unsigned)p.num_merge_tiles, PMERGE_NT, 0, st>>>(
+          kb[cur], vb[cur], kb[cur ^ 1], vb[cur ^ 1], n, run, split,
+          pass == p.merge_passes - 1 ? dt : DT_U32);
+    }
     rc = launch_status("merge_pairs");
     cur ^= 1;
   }

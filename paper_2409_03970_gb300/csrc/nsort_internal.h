@@ -36,6 +36,28 @@ int sort_pairs_impl(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, ui
 
 size_t segmented_temp_bytes(int kind, uint64_t n, uint64_t nseg);
 
+// Kernel ids of the tracer (order of its name table).
+enum TraceKernel {
+  TK_TILE_SORT_KEYS = 0, TK_TILE_SORT_PAIRS, TK_PARTITION, TK_MERGE_KEYS, TK_MERGE_PAIRS,
+  TK_SEG_BIN, TK_SEG_SORT, TK_SEG_MERGE, TK_SEG_COPY
+};
+
+// Brackets one kernel launch with CUDA events on its stream while tracing
+// is enabled (nsort_trace_enable); does nothing otherwise.
+class TraceScope {
+ public:
+  TraceScope(int kernel, cudaStream_t st);
+  ~TraceScope();
+  TraceScope(const TraceScope &) = delete;
+  TraceScope &operator=(const TraceScope &) = delete;
+
+ private:
+  int kernel_;
+  cudaStream_t st_;
+  cudaEvent_t start_ = nullptr, stop_ = nullptr;
+  bool active_ = false;
+};
+
 void set_last_error(const std::string &msg);
 const char *last_error_cstr();
 

@@ -55,6 +55,10 @@ def _load():
         lib.nsort_keys.restype = i32
         lib.nsort_pairs.argtypes = [vp, vp, vp, vp, u64, i32, vp, sz, vp]
         lib.nsort_pairs.restype = i32
+        lib.nsort_trace_enable.argtypes = [i32]
+        lib.nsort_trace_enable.restype = i32
+        lib.nsort_trace_read.argtypes = [vp, i32, ip]
+        lib.nsort_trace_read.restype = i32
         lib.nsort_status_string.argtypes = [i32]
         lib.nsort_status_string.restype = ctypes.c_char_p
         lib.nsort_last_error.argtypes = []
@@ -127,6 +131,27 @@ def nsort_pairs(keys_in, vals_in, keys_out, vals_out, n: int, dtype: int, tmp, t
                 stream=None) -> int:
     return _load().nsort_pairs(_ptr(keys_in), _ptr(vals_in), _ptr(keys_out), _ptr(vals_out), n,
                                dtype, _ptr(tmp), tmp_bytes, _stream(stream))
+
+
+class TraceEntry(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_char * 32), ("launches", ctypes.c_uint64),
+                ("total_ms", ctypes.c_double)]
+
+
+def nsort_trace_enable(on: bool) -> int:
+    return _load().nsort_trace_enable(1 if on else 0)
+
+
+def nsort_trace_read() -> dict:
+    """{kernel name: {"launches": L, "total_ms": T}} since tracing was enabled."""
+    buf = (TraceEntry * 32)()
+    cnt = ctypes.c_int()
+    rc = _load().nsort_trace_read(ctypes.addressof(buf), 32, ctypes.byref(cnt))
+    if rc != OK:
+        raise NsortError(rc, "nsort_trace_read")
+    return {buf[i].kernel.decode(): {"launches": int(buf[i].launches),
+                                     "total_ms": float(buf[i].total_ms)}
+            for i in range(min(cnt.value, 32))}
 
 
 # ---- conveniences -----------------------------------------------------------
