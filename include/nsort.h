@@ -95,6 +95,28 @@ int nsort_pairs(const void *d_keys_in, const uint32_t *d_vals_in,
                 void *d_keys_out, uint32_t *d_vals_out, uint64_t n, int dtype,
                 void *d_tmp, size_t tmp_bytes, void *stream);
 
+/* Allocation-free key sort, for callers that cannot allocate device memory:
+ * their device memory is owned by another allocator (a framework's caching
+ * pool, a fixed arena sized at start-up) or they run where a cudaMalloc is
+ * not allowed because it may block or synchronise the device.  Same result
+ * as nsort_keys, but no scratch argument: the scratch is one fixed array in
+ * the library's device global memory (about 4.03 MiB), present on every GPU
+ * that loads the library until the process exits.  The paper has no
+ * counterpart; this is an interface for such callers.
+ *  - n up to NSORT_NOALLOC_MAX_KEYS; larger n returns NSORT_ENOMEM with an
+ *    explanation in nsort_last_error().  Other errors as nsort_keys.
+ *  - Calls nothing that allocates (no cudaMalloc / cudaFree).
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress, with that device current); make that first call
+ *    before any stream capture.
+ *  - All calls on a device share the one array, which keeps whatever the last
+ *    call left in it (nothing in it needs to start at zero).  Calls whose
+ *    work overlaps on the GPU race on it: issue them on one stream, or order
+ *    them with events. */
+#define NSORT_NOALLOC_MAX_KEYS (1u << 20)
+int nsort_keys_noalloc(const void *d_keys_in, void *d_keys_out, uint64_t n, int dtype,
+                       void *stream);
+
 /* ---- tracing ------------------------------------------------------------
  * Per-kernel device time without a profiler.  While enabled, every kernel
  * launch of the library is bracketed by CUDA events recorded on the stream

@@ -1,0 +1,99 @@
+// nsort_keys_noalloc: the plain key sort for callers that cannot allocate
+// device memory.
+//
+// Some callers have no way to provide the scratch buffer nsort_keys wants:
+// their device memory belongs entirely to someone else's allocator (a
+// framework's caching pool, a fixed arena sized at start-up), or they run on
+// a path where a cudaMalloc is not allowed because it may block or
+// synchronise the device.  This entry point takes no scratch argument.  Its
+// scratch is a fixed array in this file, in device global memory, which
+// exists on every GPU that loads the library until the process exits.
+//
+// Host code cannot use the array's name as a device address (on the host it
+// names a stand-in), so the device address is looked up with
+// cudaGetSymbolAddress once per device, with that device current, the first
+// time the entry point runs on it.
+#include <cuda_runtime.h>
+
+#include <mutex>
+#include <string>
+
+#include "nsort.h"
+#include "nsort_internal.h"
+
+namespace nsort {
+
+namespace {
+
+// Scratch of a plain key sort of NSORT_NOALLOC_MAX_KEYS keys: one ping-pong
+// copy of the keys plus one int64 merge-path splitter per merge tile, sized
+// for merge tiles of 256 keys or more, each part rounded up to 256 bytes
+// (about 4.03 MiB in all).
+constexpr size_t kKeysBytes = size_t(NSORT_NOALLOC_MAX_KEYS) * 4;
+constexpr size_t kSplitBytes = ((NSORT_NOALLOC_MAX_KEYS / 256 + 2) * 8 + 255) / 256 * 256;
+constexpr size_t kScratchBytes = kKeysBytes + kSplitBytes;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void *g_scratch_addr[kMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device, looked up once.
+int scratch_for_current_device(void **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    set_last_error(std::string("nsort_keys_noalloc: cudaGetDevice: ") + cudaGetErrorString(e));
+    return NSORT_ECUDA;
+  }
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_last_error("nsort_keys_noalloc: device ordinal out of range");
+    return NSORT_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_scratch_addr[dev]) {
+    void *ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || ptr == nullptr) {
+      set_last_error(std::string("nsort_keys_noalloc: cudaGetSymbolAddress: ") +
+                     cudaGetErrorString(e));
+      return NSORT_ECUDA;
+    }
+    g_scratch_addr[dev] = ptr;
+  }
+  *out = g_scratch_addr[dev];
+  return NSORT_OK;
+}
+
+}  // namespace
+
+}  // namespace nsort
+
+using namespace nsort;
+
+extern "C" int nsort_keys_noalloc(const void *d_keys_in, void *d_keys_out, uint64_t n,
+                                  int dtype, void *stream) {
+  if (dtype != NSORT_U32 && dtype != NSORT_I32 && dtype != NSORT_F32) return NSORT_EINVAL;
+  if (n == 0) return NSORT_OK;
+  if (n > NSORT_NOALLOC_MAX_KEYS) {
+    set_last_error("nsort_keys_noalloc: n exceeds the maximum of NSORT_NOALLOC_MAX_KEYS (2^20) "
+                   "keys; use nsort_keys with a caller-provided scratch buffer");
+    return NSORT_ENOMEM;
+  }
+  if (!d_keys_in || !d_keys_out) return NSORT_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(d_keys_in) | reinterpret_cast<uintptr_t>(d_keys_out)) & 3)
+    return NSORT_EINVAL;
+  if (make_plan(NSORT_KIND_KEYS, n).total > kScratchBytes) {
+    set_last_error("nsort_keys_noalloc: internal scratch size mismatch");
+    return NSORT_ENOMEM;
+  }
+  void *scratch = nullptr;
+  const int rc = scratch_for_current_device(&scratch);
+  if (rc != NSORT_OK) return rc;
+  // Nothing in the scratch has to start at zero: the tile sort writes the
+  // whole key buffer and every pass writes its splitters before reading them.
+  return sort_keys_impl(static_cast<const uint32_t *>(d_keys_in),
+                        static_cast<uint32_t *>(d_keys_out), (int64_t)n, dtype, scratch,
+                        static_cast<cudaStream_t>(stream));
+}

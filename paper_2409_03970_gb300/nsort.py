@@ -55,6 +55,8 @@ def _load():
         lib.nsort_keys.restype = i32
         lib.nsort_pairs.argtypes = [vp, vp, vp, vp, u64, i32, vp, sz, vp]
         lib.nsort_pairs.restype = i32
+        lib.nsort_keys_noalloc.argtypes = [vp, vp, u64, i32, vp]
+        lib.nsort_keys_noalloc.restype = i32
         lib.nsort_trace_enable.argtypes = [i32]
         lib.nsort_trace_enable.restype = i32
         lib.nsort_trace_read.argtypes = [vp, i32, ip]
@@ -131,6 +133,16 @@ def nsort_pairs(keys_in, vals_in, keys_out, vals_out, n: int, dtype: int, tmp, t
                 stream=None) -> int:
     return _load().nsort_pairs(_ptr(keys_in), _ptr(vals_in), _ptr(keys_out), _ptr(vals_out), n,
                                dtype, _ptr(tmp), tmp_bytes, _stream(stream))
+
+
+NOALLOC_MAX_KEYS = 1 << 20
+
+
+def nsort_keys_noalloc(keys_in, keys_out, n: int, dtype: int, stream=None) -> int:
+    """nsort_keys without a scratch argument, for callers that cannot
+    allocate device memory (scratch is a fixed array inside the library;
+    n <= NOALLOC_MAX_KEYS; calls that overlap on the GPU race on it)."""
+    return _load().nsort_keys_noalloc(_ptr(keys_in), _ptr(keys_out), n, dtype, _stream(stream))
 
 
 class TraceEntry(ctypes.Structure):
