@@ -95,6 +95,47 @@ int nsort_pairs(const void *d_keys_in, const uint32_t *d_vals_in,
                 void *d_keys_out, uint32_t *d_vals_out, uint64_t n, int dtype,
                 void *d_tmp, size_t tmp_bytes, void *stream);
 
+/* Segmented sort: nseg independent arrays stored back to back.  d_offsets
+ * is a DEVICE array of nseg+1 int64 (CSR form): segment s is
+ * [d_offsets[s], d_offsets[s+1]), d_offsets[0] == 0, non-decreasing,
+ * d_offsets[nseg] == n (the total key count).  Empty segments are allowed.
+ * Each segment is sorted on its own as nsort_keys / nsort_pairs would sort
+ * it (stable when values are given; d_vals_in and d_vals_out both NULL for
+ * keys only).  The batch runs as three small set-up kernels (binning by
+ * length on the device) and one persistent kernel that takes segments from
+ * a work queue: one thread per segment of at most `tiny_width` keys, one
+ * warp per segment of at most 32 x `small_ipt`, one CTA per segment of at
+ * most one tile, and tile sorts plus merge levels for longer ones.  Every
+ * step is stream-ordered with no host synchronisation, so the call can be
+ * captured into a CUDA graph.  Scratch:
+ * nsort_temp_bytes(NSORT_KIND_SEGMENTED[_PAIRS], n, nseg, dtype), 256-byte
+ * aligned; in-place (in == out) is allowed.  Host-checked errors:
+ * NSORT_EINVAL, NSORT_ENOMEM, NSORT_ECUDA.  Malformed offsets are found on
+ * the device: the batch is left unsorted and nsort_segmented_status()
+ * reports NSORT_EINVAL.  Source: the paper's sort (Sec. 2.1) applied per
+ * segment; the batching is this library's extension. */
+int nsort_segmented(const void *d_keys_in, void *d_keys_out,
+                    const uint32_t *d_vals_in, uint32_t *d_vals_out,
+                    const int64_t *d_offsets, uint64_t nseg, uint64_t n, int dtype,
+                    void *d_tmp, size_t tmp_bytes, void *stream);
+
+/* Synchronises `stream` and returns the device-side status of the last
+ * nsort_segmented call that used d_tmp: NSORT_OK, NSORT_EINVAL (malformed
+ * offsets) or NSORT_ETIMEOUT (a merge level waited too long for its inputs;
+ * the result is then incomplete). */
+int nsort_segmented_status(const void *d_tmp, void *stream);
+
+/* Tunables of nsort_segmented, set by the autotuner (process-wide). */
+typedef struct {
+    int block_threads;   /* 256 or 512: persistent CTA size; tile = 16 x block_threads keys */
+    int tiny_width;      /* 8 or 16: network width of the one-thread bin */
+    int small_ipt;       /* 8 or 16: keys per lane of the one-warp bin */
+    int blocks_per_sm;   /* persistent CTAs per SM; 0 = as many as fit */
+} nsort_seg_config;
+
+int nsort_segmented_set_config(const nsort_seg_config *cfg);
+int nsort_segmented_get_config(nsort_seg_config *cfg);
+
 /* Allocation-free key sort, for callers that cannot allocate device memory:
  * their device memory is owned by another allocator (a framework's caching
  * pool, a fixed arena sized at start-up) or they run where a cudaMalloc is

@@ -30,85 +30,89 @@ namespace nsort {
 // ---------------------------------------------------------------- kernels
 
 // Sorts one tile of NT*16 elements that is already in registers (16 per
-// thread, any assignment) and leaves it sorted in s (padded layout).
+// thread, any assignment).  On return thread t holds tile elements
+// [16t, 16t + 16) of the sorted tile in r.  s is scratch (merge_smem_len).
 template <int NT, typename K>
 __device__ __forceinline__ void sort_tile_in_block(K (&r)[16], K *s) {
   constexpr int TILE = NT * 16;
   const int tid = threadIdx.x;
   const int lane = tid & 31;
-  const int warp = tid >> 5;
   column_sort16(r);
   warp_merge512(r, lane);
-  const int ew = warp * 512 + lane * 16;
+  if (TILE == 512) return;
+  const int e0 = tid * 16;
 #pragma unroll
-  for (int k = 0; k < 16; ++k) s[pidx<K>(ew + k)] = r[k];
+  for (int k = 0; k < 16; ++k) s[pidx<K>(e0 + k)] = r[k];
   int unused[16];
 #pragma unroll 1
   for (int run = 512; run < TILE; run <<= 1) {
     __syncthreads();
-    const int e0 = tid * 16;
     const int g0 = e0 & ~(2 * run - 1);
     const int diag = e0 - g0;
     const int ai = merge_path_smem(s, g0, run, g0 + run, run, diag);
-    serial_merge<16, false>(s, g0 + ai, g0 + run, g0 + run + diag - ai, g0 + 2 * run,
-                            TILE - 1, r, unused);
-    __syncthreads();
+    serial_merge<16, false>(s, g0 + ai, g0 + run, g0 + run + diag - ai, g0 + 2 * run, r, unused);
+    if (2 * run < TILE) {
+      __syncthreads();
 #pragma unroll
-    for (int k = 0; k < 16; ++k) s[pidx<K>(e0 + k)] = r[k];
+      for (int k = 0; k < 16; ++k) s[pidx<K>(e0 + k)] = r[k];
+    }
   }
-  __syncthreads();
 }
 
-// Stores `count` sorted keys from s (padded layout) to out, mapping each
-// key back to its bit pattern with dt_out (DT_U32 = leave as is).
-template <int NT, int VT>
-__device__ __forceinline__ void store_keys(const uint32_t *s, uint32_t *out, int count,
-                                           int dt_out) {
-  constexpr int TILE = NT * VT;
-  const int tid = threadIdx.x;
-  if (count == TILE && !(reinterpret_cast<uintptr_t>(out) & 15)) {
+// Thread t stores its VT consecutive outputs o[] at out[t*VT ...], mapped
+// back to bit patterns by DT_OUT.  Full, 16-byte aligned tiles use 128-bit
+// stores straight from registers; others store element by element.
+template <int VT, int DT_OUT>
+__device__ __forceinline__ void store_run(const uint32_t (&o)[VT], uint32_t *tile_out, int count,
+                                          bool full) {
+  const int e0 = threadIdx.x * VT;
+  uint32_t *out = tile_out + e0;
+  if (full) {
 #pragma unroll
-    for (int j = 0; j < VT / 4; ++j) {
-      const int c = tid + NT * j;
-      const int e = 4 * c;
+    for (int q = 0; q < VT / 4; ++q) {
       uint4 v;
-      v.x = from_key(s[pidx<uint32_t>(e)], dt_out);
-      v.y = from_key(s[pidx<uint32_t>(e + 1)], dt_out);
-      v.z = from_key(s[pidx<uint32_t>(e + 2)], dt_out);
-      v.w = from_key(s[pidx<uint32_t>(e + 3)], dt_out);
-      reinterpret_cast<uint4 *>(out)[c] = v;
+      v.x = from_key(o[4 * q + 0], DT_OUT);
+      v.y = from_key(o[4 * q + 1], DT_OUT);
+      v.z = from_key(o[4 * q + 2], DT_OUT);
+      v.w = from_key(o[4 * q + 3], DT_OUT);
+      reinterpret_cast<uint4 *>(out)[q] = v;
     }
   } else {
 #pragma unroll
-    for (int j = 0; j < VT; ++j) {
-      const int e = tid + NT * j;
-      if (e < count) out[e] = from_key(s[pidx<uint32_t>(e)], dt_out);
-    }
+    for (int k = 0; k < VT; ++k)
+      if (e0 + k < count) out[k] = from_key(o[k], DT_OUT);
   }
 }
 
-// Tile sort, keys only.  Tile t covers [t*TILE, min((t+1)*TILE, n)); a short
+__device__ __forceinline__ bool aligned16(const void *p) {
+  return !(reinterpret_cast<uintptr_t>(p) & 15);
+}
+
+// Tile sort, keys only.  Tile b covers [b*TILE, min((b+1)*TILE, n)); a short
 // last tile is padded with the largest key, which sorts behind every real
-// key and is never stored.  in may equal out (each CTA reads its whole tile
-// before the first barrier and writes it after the last).
-template <int NT>
+// key and is never stored.  DT is the key type (its order-preserving map is
+// applied on load); FINAL maps the keys back on store (the tile sort is the
+// whole sort when n fits one tile).  in may equal out: each CTA reads its
+// whole tile before its first barrier and writes it after its last.
+template <int NT, int DT, bool FINAL>
 __global__ void __launch_bounds__(NT) tile_sort_keys_kernel(const uint32_t *in, uint32_t *out,
-                                                            int64_t n, int dt, int dt_out) {
+                                                            int64_t n) {
   constexpr int TILE = NT * 16;
-  __shared__ uint32_t s[padded_len<uint32_t>(TILE)];
+  __shared__ uint32_t s[merge_smem_len<uint32_t>(TILE, 16)];
   const int tid = threadIdx.x;
   const int64_t base = (int64_t)blockIdx.x * TILE;
   const int count = (int)(n - base < TILE ? n - base : TILE);
+  const bool full = count == TILE && aligned16(in + base) && aligned16(out + base);
   uint32_t r[16];
-  if (count == TILE && !(reinterpret_cast<uintptr_t>(in + base) & 15)) {
+  if (full) {
     const uint4 *p = reinterpret_cast<const uint4 *>(in + base);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const uint4 v = p[tid + NT * j];
-      r[4 * j + 0] = to_key(v.x, dt);
-      r[4 * j + 1] = to_key(v.y, dt);
-      r[4 * j + 2] = to_key(v.z, dt);
-      r[4 * j + 3] = to_key(v.w, dt);
+      r[4 * j + 0] = to_key(v.x, DT);
+      r[4 * j + 1] = to_key(v.y, DT);
+      r[4 * j + 2] = to_key(v.z, DT);
+      r[4 * j + 3] = to_key(v.w, DT);
     }
   } else {
 #pragma unroll
@@ -116,27 +120,27 @@ __global__ void __launch_bounds__(NT) tile_sort_keys_kernel(const uint32_t *in, 
 #pragma unroll
       for (int w = 0; w < 4; ++w) {
         const int e = 4 * (tid + NT * j) + w;
-        r[4 * j + w] = e < count ? to_key(in[base + e], dt) : 0xFFFFFFFFu;
+        r[4 * j + w] = e < count ? to_key(in[base + e], DT) : 0xFFFFFFFFu;
       }
     }
   }
   sort_tile_in_block<NT>(r, s);
-  store_keys<NT, 16>(s, out + base, count, dt_out);
+  store_run<16, FINAL ? DT : DT_U32>(r, out + base, count, full);
 }
 
 // Tile sort, key/value pairs.  The networks sort 64-bit composites
 // (key << 32 | position in tile); positions make every composite distinct,
 // so the network's result is the stable order.  Values are staged in shared
 // memory and gathered by position at the end.
-template <int NT>
+template <int NT, int DT, bool FINAL>
 __global__ void __launch_bounds__(NT) tile_sort_pairs_kernel(const uint32_t *kin,
                                                              const uint32_t *vin,
                                                              uint32_t *kout, uint32_t *vout,
-                                                             int64_t n, int dt, int dt_out) {
+                                                             int64_t n) {
   constexpr int TILE = NT * 16;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   uint64_t *s = reinterpret_cast<uint64_t *>(smem_raw);
-  uint32_t *sv = reinterpret_cast<uint32_t *>(s + padded_len<uint64_t>(TILE));
+  uint32_t *sv = reinterpret_cast<uint32_t *>(s + merge_smem_len<uint64_t>(TILE, 16));
   const int tid = threadIdx.x;
   const int64_t base = (int64_t)blockIdx.x * TILE;
   const int count = (int)(n - base < TILE ? n - base : TILE);
@@ -151,29 +155,28 @@ __global__ void __launch_bounds__(NT) tile_sort_pairs_kernel(const uint32_t *kin
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
       const int e = 4 * (tid + NT * j) + w;
-      r[4 * j + w] = e < count ? ((uint64_t)to_key(kin[base + e], dt) << 32) | (uint32_t)e
+      r[4 * j + w] = e < count ? ((uint64_t)to_key(kin[base + e], DT) << 32) | (uint32_t)e
                                : ~0ull;
     }
   }
   sort_tile_in_block<NT>(r, s);
+  // every thread passed a barrier after the values were staged
+  uint32_t ko[16], vo[16];
 #pragma unroll
-  for (int j = 0; j < 16; ++j) {
-    const int e = tid + NT * j;
-    if (e < count) {
-      const uint64_t c = s[pidx<uint64_t>(e)];
-      kout[base + e] = from_key((uint32_t)(c >> 32), dt_out);
-      vout[base + e] = sv[pidx<uint32_t>((int)(c & 0xFFFFu))];
-    }
+  for (int k = 0; k < 16; ++k) {
+    ko[k] = (uint32_t)(r[k] >> 32);
+    vo[k] = sv[pidx<uint32_t>((int)(r[k] & 0xFFFFu) & (TILE - 1))];
   }
+  const bool full = count == TILE && aligned16(kout + base) && aligned16(vout + base);
+  store_run<16, FINAL ? DT : DT_U32>(ko, kout + base, count, full);
+  store_run<16, DT_U32>(vo, vout + base, count, full);
 }
 
 // Which slices of the two input runs one merge CTA consumes.
 struct PassTile {
   int64_t out0;      // first output element of the tile
-  int64_t pair0;     // first element of the run pair (A then B)
-  int64_t la;        // length of run A
-  int64_t a_beg;     // slice of A: [a_beg, a_beg + na)
-  int64_t b_beg;     // slice of B: [b_beg, b_beg + nb)
+  int64_t a_off;     // global index of the first element of the A slice
+  int64_t b_off;     // global index of the first element of the B slice
   int na, nb, count;
 };
 
@@ -182,22 +185,24 @@ __device__ __forceinline__ PassTile pass_tile(int64_t n, int64_t run, int tile,
   PassTile g;
   g.out0 = (int64_t)blockIdx.x * tile;
   const int64_t out1 = g.out0 + tile < n ? g.out0 + tile : n;
-  g.pair0 = g.out0 & ~(2 * run - 1);
-  g.la = n - g.pair0 < run ? n - g.pair0 : run;
-  const int64_t rest = n - g.pair0 - run;
+  const int64_t pair0 = g.out0 & ~(2 * run - 1);
+  const int64_t la = n - pair0 < run ? n - pair0 : run;
+  const int64_t rest = n - pair0 - run;
   const int64_t lb = rest <= 0 ? 0 : (rest < run ? rest : run);
-  const int64_t pair_end = g.pair0 + g.la + lb;
-  const int64_t a_end = out1 == pair_end ? g.la : split[blockIdx.x + 1];
-  g.a_beg = split[blockIdx.x];
-  g.b_beg = (g.out0 - g.pair0) - g.a_beg;
-  const int64_t b_end = (out1 - g.pair0) - a_end;
-  g.na = (int)(a_end - g.a_beg);
-  g.nb = (int)(b_end - g.b_beg);
+  const int64_t pair_end = pair0 + la + lb;
+  const int64_t a_end = out1 == pair_end ? la : split[blockIdx.x + 1];
+  const int64_t a_beg = split[blockIdx.x];
+  const int64_t b_beg = (g.out0 - pair0) - a_beg;
+  const int64_t b_end = (out1 - pair0) - a_end;
+  g.a_off = pair0 + a_beg;
+  g.b_off = pair0 + la + b_beg;
+  g.na = (int)(a_end - a_beg);
+  g.nb = (int)(b_end - b_beg);
   g.count = g.na + g.nb;
   return g;
 }
 
-// Merge-path splitters of one pass: for every output tile, how many
+// Merge-path splitters of one pass, one thread per output tile: how many
 // elements of its pair's A run precede the tile (stable: A wins ties).
 __global__ void partition_kernel(const uint32_t *__restrict__ src, int64_t n, int64_t run,
                                  int tile, int64_t num_tiles, int64_t *__restrict__ split) {
@@ -211,87 +216,80 @@ __global__ void partition_kernel(const uint32_t *__restrict__ src, int64_t n, in
   split[t] = merge_path_global(src + pair0, la, src + pair0 + la, lb, out0 - pair0);
 }
 
-// One merge pass over keys: CTA b produces output tile b.
-template <int NT, int VT>
-__global__ void __launch_bounds__(NT) merge_keys_kernel(const uint32_t *__restrict__ src,
-                                                        uint32_t *__restrict__ dst, int64_t n,
-                                                        int64_t run,
-                                                        const int64_t *__restrict__ split,
-                                                        int dt_out) {
-  constexpr int TILE = NT * VT;
-  __shared__ uint32_t s[padded_len<uint32_t>(TILE)];
+// Stages the merge inputs of one tile, A slice then B slice, into
+// s[0, count) (padded layout).  Element i = tid + NT*j of the tile comes
+// from A[i] or B[i - na]; all loads are issued before the shared stores.
+template <int NT, int VT, typename T>
+__device__ __forceinline__ void stage_slices(T *s, const T *__restrict__ src, int64_t a_off,
+                                             int64_t b_off, int na, int count) {
+  static_assert(NT % 32 == 0, "NT must be a multiple of the warp size");
   const int tid = threadIdx.x;
-  const PassTile g = pass_tile(n, run, TILE, split);
-  const uint32_t *A = src + g.pair0 + g.a_beg;
-  const uint32_t *B = src + g.pair0 + g.la + g.b_beg;
-  uint32_t t[VT];
+  const T *pa = src + a_off + tid;
+  const T *pb = src + b_off + (tid - na);
+  T t[VT];
 #pragma unroll
   for (int j = 0; j < VT; ++j) {
     const int i = tid + NT * j;
-    t[j] = i < g.na ? A[i] : (i < g.count ? B[i - g.na] : 0u);
+    T v = 0;
+    if (i < na) v = __ldg(pa + NT * j);
+    else if (i < count) v = __ldg(pb + NT * j);
+    t[j] = v;
   }
+  const int sbase = pidx<T>(tid);
 #pragma unroll
-  for (int j = 0; j < VT; ++j) s[pidx<uint32_t>(tid + NT * j)] = t[j];
+  for (int j = 0; j < VT; ++j) s[sbase + j * (NT + (NT >> Pad<T>::SHIFT))] = t[j];
+}
+
+// One merge pass over keys: CTA b produces output tile b.  DT_OUT maps the
+// keys back to bit patterns (last pass only).
+template <int NT, int VT, int DT_OUT>
+__global__ void __launch_bounds__(NT, 6) merge_keys_kernel(const uint32_t *__restrict__ src,
+                                                           uint32_t *__restrict__ dst, int64_t n,
+                                                           int64_t run,
+                                                           const int64_t *__restrict__ split) {
+  constexpr int TILE = NT * VT;
+  __shared__ uint32_t s[merge_smem_len<uint32_t>(TILE, VT)];
+  const int tid = threadIdx.x;
+  const PassTile g = pass_tile(n, run, TILE, split);
+  stage_slices<NT, VT>(s, src, g.a_off, g.b_off, g.na, g.count);
   __syncthreads();
   const int diag = tid * VT < g.count ? tid * VT : g.count;
   const int ai = merge_path_smem(s, 0, g.na, g.na, g.nb, diag);
   uint32_t o[VT];
   int unused[VT];
-  serial_merge<VT, false>(s, ai, g.na, g.na + diag - ai, g.count, TILE - 1, o, unused);
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < VT; ++k) s[pidx<uint32_t>(tid * VT + k)] = o[k];
-  __syncthreads();
-  store_keys<NT, VT>(s, dst + g.out0, g.count, dt_out);
+  serial_merge<VT, false>(s, ai, g.na, g.na + diag - ai, g.count, o, unused);
+  uint32_t *out = dst + g.out0;
+  store_run<VT, DT_OUT>(o, out, g.count, g.count == TILE && aligned16(out));
 }
 
 // One merge pass over key/value pairs (stable).
-template <int NT, int VT>
-__global__ void __launch_bounds__(NT) merge_pairs_kernel(const uint32_t *__restrict__ ksrc,
-                                                         const uint32_t *__restrict__ vsrc,
-                                                         uint32_t *__restrict__ kdst,
-                                                         uint32_t *__restrict__ vdst,
-                                                         int64_t n, int64_t run,
-                                                         const int64_t *__restrict__ split,
-                                                         int dt_out) {
+template <int NT, int VT, int DT_OUT>
+__global__ void __launch_bounds__(NT, 3) merge_pairs_kernel(const uint32_t *__restrict__ ksrc,
+                                                            const uint32_t *__restrict__ vsrc,
+                                                            uint32_t *__restrict__ kdst,
+                                                            uint32_t *__restrict__ vdst,
+                                                            int64_t n, int64_t run,
+                                                            const int64_t *__restrict__ split) {
   constexpr int TILE = NT * VT;
-  __shared__ uint32_t sk[padded_len<uint32_t>(TILE)];
-  __shared__ uint32_t sv[padded_len<uint32_t>(TILE)];
+  __shared__ uint32_t sk[merge_smem_len<uint32_t>(TILE, VT)];
+  __shared__ uint32_t sv[merge_smem_len<uint32_t>(TILE, VT)];
   const int tid = threadIdx.x;
   const PassTile g = pass_tile(n, run, TILE, split);
-  const int64_t a_off = g.pair0 + g.a_beg;
-  const int64_t b_off = g.pair0 + g.la + g.b_beg;
-  uint32_t tk[VT], tv[VT];
-#pragma unroll
-  for (int j = 0; j < VT; ++j) {
-    const int i = tid + NT * j;
-    const int64_t at = i < g.na ? a_off + i : b_off + (i - g.na);
-    const bool ok = i < g.count;
-    tk[j] = ok ? ksrc[at] : 0u;
-    tv[j] = ok ? vsrc[at] : 0u;
-  }
-#pragma unroll
-  for (int j = 0; j < VT; ++j) {
-    sk[pidx<uint32_t>(tid + NT * j)] = tk[j];
-    sv[pidx<uint32_t>(tid + NT * j)] = tv[j];
-  }
+  stage_slices<NT, VT>(sk, ksrc, g.a_off, g.b_off, g.na, g.count);
+  stage_slices<NT, VT>(sv, vsrc, g.a_off, g.b_off, g.na, g.count);
   __syncthreads();
   const int diag = tid * VT < g.count ? tid * VT : g.count;
   const int ai = merge_path_smem(sk, 0, g.na, g.na, g.nb, diag);
-  uint32_t o[VT];
+  uint32_t o[VT], ov[VT];
   int from[VT];
-  serial_merge<VT, true>(sk, ai, g.na, g.na + diag - ai, g.count, TILE - 1, o, from);
+  serial_merge<VT, true>(sk, ai, g.na, g.na + diag - ai, g.count, o, from);
 #pragma unroll
-  for (int k = 0; k < VT; ++k) tv[k] = sv[pidx<uint32_t>(from[k] < TILE ? from[k] : TILE - 1)];
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < VT; ++k) {
-    sk[pidx<uint32_t>(tid * VT + k)] = o[k];
-    sv[pidx<uint32_t>(tid * VT + k)] = tv[k];
-  }
-  __syncthreads();
-  store_keys<NT, VT>(sk, kdst + g.out0, g.count, dt_out);
-  store_keys<NT, VT>(sv, vdst + g.out0, g.count, DT_U32);
+  for (int k = 0; k < VT; ++k) ov[k] = sv[pidx<uint32_t>(from[k])];
+  uint32_t *ko = kdst + g.out0;
+  uint32_t *vo = vdst + g.out0;
+  const bool full = g.count == TILE && aligned16(ko) && aligned16(vo);
+  store_run<VT, DT_OUT>(o, ko, g.count, full);
+  store_run<VT, DT_U32>(ov, vo, g.count, full);
 }
 
 // ------------------------------------------------------------- host side
@@ -311,7 +309,7 @@ constexpr int MERGE_TILE = MERGE_NT * MERGE_VT;
 constexpr int PMERGE_TILE = PMERGE_NT * PMERGE_VT;
 
 constexpr size_t PAIRS_SORT_SMEM =
-    sizeof(uint64_t) * padded_len<uint64_t>(PAIRS_SORT_TILE) +
+    sizeof(uint64_t) * merge_smem_len<uint64_t>(PAIRS_SORT_TILE, 16) +
     sizeof(uint32_t) * padded_len<uint32_t>(PAIRS_SORT_TILE);
 
 }  // namespace
@@ -343,19 +341,81 @@ static int launch_status(const char *what) {
   return NSORT_ECUDA;
 }
 
+// ---- template dispatch (key type and "last pass" are compile-time) -------
+
+static void launch_tile_sort_keys(const uint32_t *in, uint32_t *out, int64_t n, int dt,
+                                  bool final_pass, unsigned grid, cudaStream_t st) {
+#define NSORT_TSK(DT, FIN) \
+  tile_sort_keys_kernel<KEYS_SORT_NT, DT, FIN><<<grid, KEYS_SORT_NT, 0, st>>>(in, out, n)
+  if (dt == DT_U32) { if (final_pass) NSORT_TSK(DT_U32, true); else NSORT_TSK(DT_U32, false); }
+  else if (dt == DT_I32) { if (final_pass) NSORT_TSK(DT_I32, true); else NSORT_TSK(DT_I32, false); }
+  else { if (final_pass) NSORT_TSK(DT_F32, true); else NSORT_TSK(DT_F32, false); }
+#undef NSORT_TSK
+}
+
+static void launch_merge_keys(const uint32_t *src, uint32_t *dst, int64_t n, int64_t run,
+                              const int64_t *split, int dt_out, unsigned grid, cudaStream_t st) {
+#define NSORT_MK(DT) \
+  merge_keys_kernel<MERGE_NT, MERGE_VT, DT><<<grid, MERGE_NT, 0, st>>>(src, dst, n, run, split)
+  if (dt_out == DT_U32) NSORT_MK(DT_U32);
+  else if (dt_out == DT_I32) NSORT_MK(DT_I32);
+  else NSORT_MK(DT_F32);
+#undef NSORT_MK
+}
+
+template <int DT, bool FIN>
+static cudaError_t pairs_smem_attr() {
+  return cudaFuncSetAttribute(tile_sort_pairs_kernel<PAIRS_SORT_NT, DT, FIN>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PAIRS_SORT_SMEM);
+}
+
 static int ensure_pairs_smem_attr() {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return launch_status("cudaGetDevice");
   static std::atomic<uint64_t> done_mask{0};
   const uint64_t bit = dev < 64 ? (uint64_t(1) << dev) : 0;
   if (bit && (done_mask.load() & bit)) return NSORT_OK;
-  if (cudaFuncSetAttribute(tile_sort_pairs_kernel<PAIRS_SORT_NT>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)PAIRS_SORT_SMEM) != cudaSuccess)
-    return launch_status("cudaFuncSetAttribute");
+  cudaError_t e = pairs_smem_attr<DT_U32, false>();
+  if (e == cudaSuccess) e = pairs_smem_attr<DT_U32, true>();
+  if (e == cudaSuccess) e = pairs_smem_attr<DT_I32, false>();
+  if (e == cudaSuccess) e = pairs_smem_attr<DT_I32, true>();
+  if (e == cudaSuccess) e = pairs_smem_attr<DT_F32, false>();
+  if (e == cudaSuccess) e = pairs_smem_attr<DT_F32, true>();
+  if (e != cudaSuccess) return launch_status("cudaFuncSetAttribute");
   done_mask.fetch_or(bit);
   return NSORT_OK;
 }
+
+static void launch_tile_sort_pairs(const uint32_t *kin, const uint32_t *vin, uint32_t *kout,
+                                   uint32_t *vout, int64_t n, int dt, bool final_pass,
+                                   unsigned grid, cudaStream_t st) {
+#define NSORT_TSP(DT, FIN)                                                      \
+  tile_sort_pairs_kernel<PAIRS_SORT_NT, DT, FIN><<<grid, PAIRS_SORT_NT, PAIRS_SORT_SMEM, st>>>( \
+      kin, vin, kout, vout, n)
+  if (dt == DT_U32) { if (final_pass) NSORT_TSP(DT_U32, true); else NSORT_TSP(DT_U32, false); }
+  else if (dt == DT_I32) { if (final_pass) NSORT_TSP(DT_I32, true); else NSORT_TSP(DT_I32, false); }
+  else { if (final_pass) NSORT_TSP(DT_F32, true); else NSORT_TSP(DT_F32, false); }
+#undef NSORT_TSP
+}
+
+static void launch_merge_pairs(const uint32_t *ks, const uint32_t *vs, uint32_t *kd, uint32_t *vd,
+                               int64_t n, int64_t run, const int64_t *split, int dt_out,
+                               unsigned grid, cudaStream_t st) {
+#define NSORT_MP(DT) \
+  merge_pairs_kernel<PMERGE_NT, PMERGE_VT, DT><<<grid, PMERGE_NT, 0, st>>>(ks, vs, kd, vd, n, run, split)
+  if (dt_out == DT_U32) NSORT_MP(DT_U32);
+  else if (dt_out == DT_I32) NSORT_MP(DT_I32);
+  else NSORT_MP(DT_F32);
+#undef NSORT_MP
+}
+
+static void launch_partition(const uint32_t *src, int64_t n, int64_t run, const Plan &p,
+                             int64_t *split, cudaStream_t st) {
+  const unsigned blocks = (unsigned)((p.num_merge_tiles + 255) / 256);
+  partition_kernel<<<blocks, 256, 0, st>>>(src, n, run, p.merge_tile, p.num_merge_tiles, split);
+}
+
+// ---- the sorts ------------------------------------------------------------
 
 int sort_keys_impl(const uint32_t *in, uint32_t *out, int64_t n, int dt, void *tmp,
                    cudaStream_t st) {
@@ -368,22 +428,19 @@ int sort_keys_impl(const uint32_t *in, uint32_t *out, int64_t n, int dt, void *t
   const int64_t tiles = (n + p.sort_tile - 1) / p.sort_tile;
   {
     TraceScope tr(TK_TILE_SORT_KEYS, st);
-    tile_sort_keys_kernel<KEYS_SORT_NT><<<(unsigned)tiles, KEYS_SORT_NT, 0, st>>>(
-        in, bufs[cur], n, dt, p.merge_passes == 0 ? dt : DT_U32);
+    launch_tile_sort_keys(in, bufs[cur], n, dt, p.merge_passes == 0, (unsigned)tiles, st);
   }
   int rc = launch_status("tile_sort_keys");
   for (int pass = 0; rc == NSORT_OK && pass < p.merge_passes; ++pass) {
     const int64_t run = (int64_t)p.sort_tile << pass;
-    const unsigned pblocks = (unsigned)((p.num_merge_tiles + 255) / 256);
     {
       TraceScope tr(TK_PARTITION, st);
-      partition_kernel<<<pblocks, 256, 0, st>>>(bufs[cur], n, run, p.merge_tile,
-                                                p.num_merge_tiles, split);
+      launch_partition(bufs[cur], n, run, p, split, st);
     }
     {
       TraceScope tr(TK_MERGE_KEYS, st);
-      merge_keys_kernel<MERGE_NT, MERGE_VT><<<(unsigned)p.num_merge_tiles, MERGE_NT, 0, st>>>(
-          bufs[cur], bufs[cur ^ 1], n, run, split, pass == p.merge_passes - 1 ? dt : DT_U32);
+      launch_merge_keys(bufs[cur], bufs[cur ^ 1], n, run, split,
+                        pass == p.merge_passes - 1 ? dt : DT_U32, (unsigned)p.num_merge_tiles, st);
     }
     rc = launch_status("merge_keys");
     cur ^= 1;
@@ -404,23 +461,20 @@ int sort_pairs_impl(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, ui
   const int64_t tiles = (n + p.sort_tile - 1) / p.sort_tile;
   {
     TraceScope tr(TK_TILE_SORT_PAIRS, st);
-    tile_sort_pairs_kernel<PAIRS_SORT_NT><<<(unsigned)tiles, PAIRS_SORT_NT, PAIRS_SORT_SMEM, st>>>(
-        kin, vin, kb[cur], vb[cur], n, dt, p.merge_passes == 0 ? dt : DT_U32);
+    launch_tile_sort_pairs(kin, vin, kb[cur], vb[cur], n, dt, p.merge_passes == 0,
+                           (unsigned)tiles, st);
   }
   rc = launch_status("tile_sort_pairs");
   for (int pass = 0; rc == NSORT_OK && pass < p.merge_passes; ++pass) {
     const int64_t run = (int64_t)p.sort_tile << pass;
-    const unsigned pblocks = (unsigned)((p.num_merge_tiles + 255) / 256);
     {
       TraceScope tr(TK_PARTITION, st);
-      partition_kernel<<<pblocks, 256, 0, st>>>(kb[cur], n, run, p.merge_tile,
-                                                p.num_merge_tiles, split);
+      launch_partition(kb[cur], n, run, p, split, st);
     }
     {
       TraceScope tr(TK_MERGE_PAIRS, st);
-      merge_pairs_kernel<PMERGE_NT, PMERGE_VT><<<(unsigned)p.num_merge_tiles, PMERGE_NT, 0, st>>>(
-          kb[cur], vb[cur], kb[cur ^ 1], vb[cur ^ 1], n, run, split,
-          pass == p.merge_passes - 1 ? dt : DT_U32);
+      launch_merge_pairs(kb[cur], vb[cur], kb[cur ^ 1], vb[cur ^ 1], n, run, split,
+                         pass == p.merge_passes - 1 ? dt : DT_U32, (unsigned)p.num_merge_tiles, st);
     }
     rc = launch_status("merge_pairs");
     cur ^= 1;

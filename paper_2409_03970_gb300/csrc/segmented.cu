@@ -1,0 +1,651 @@
+// nsort_segmented: many independent arrays sorted in one persistent launch.
+//
+// Segments are binned by length on the device:
+//   tiny   L <= W_t          one thread sorts the segment in registers with
+//                            the W_t-input network (W_t = 8 or 16);
+//   small  L <= 32 * IPT     one warp: column sort of IPT keys per lane and
+//                            the warp flip merger (IPT = 8 or 16);
+//   medium L <= TILE         one CTA: tile sort with the active size rounded
+//                            up to a power of two;
+//   large  L >  TILE         tile sorts of the segment's TILE-key tiles
+//                            (level 0), then one merge level per doubling of
+//                            the run length, each split into TILE-output
+//                            merge tiles with their own merge-path splitters.
+// A persistent kernel takes work items from a queue (one atomic counter):
+// [level-0 tiles of all large segments][medium][small batches][tiny
+// batches][level-1 merge tiles][level-2]...  A merge tile of level k waits
+// until every level k-1 item of its segment has finished (a per-segment
+// counter with bounded waiting).  Items are taken in queue order and only
+// wait on items earlier in the queue, which are already held by running
+// CTAs, so the waits always end.
+//
+// The tunables (block size NT, tiny network width W_t, small-bin IPT, CTAs
+// per SM) come from nsort_segmented_set_config, fed by the autotuner.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <mutex>
+#include <string>
+#include <type_traits>
+
+#include "nsort.h"
+#include "nsort_internal.h"
+#include "sort_device.cuh"
+
+namespace nsort {
+namespace seg {
+
+constexpr int MAXLV = 40;          // merge levels a segment can need (2^40 keys / 4096)
+constexpr int MIN_TILE = 256 * 16; // smallest tile over the configurations
+
+struct Ctrl {
+  int status;                          // NSORT_OK, NSORT_EINVAL (offsets), NSORT_ETIMEOUT
+  int max_level;
+  unsigned long long next_item;        // queue head
+  unsigned long long n_tiny, n_small, n_medium;
+  unsigned long long bucket_tiles[MAXLV + 1];   // tiles of large segments needing b levels
+  unsigned long long bucket_base[MAXLV + 2];    // exclusive prefix of bucket_tiles
+  unsigned long long q_medium, q_small, q_tiny, q_merge, q_total;
+  unsigned long long q_level[MAXLV + 2];        // first queue item of merge level k >= 1
+};
+
+struct Params {
+  const uint32_t *kin;
+  uint32_t *kout;
+  const uint32_t *vin;   // nullptr: keys only
+  uint32_t *vout;
+  uint32_t *ktmp;
+  uint32_t *vtmp;
+  const int64_t *off;
+  int64_t nseg;
+  int64_t n;
+  Ctrl *ctrl;
+  int *tiny_list;
+  int *small_list;
+  int *medium_list;
+  int64_t *slot_base;    // large segment -> first slot of its tiles
+  unsigned long long *done;   // large segment -> finished items
+  int *owner;            // slot -> large segment
+  int dt;
+  int tile;              // NT * 16
+  int nt;
+  int tiny_w;            // 8 or 16
+  int small_ipt;         // 8 or 16
+};
+
+__device__ __forceinline__ int ceil_log2(int64_t x) {
+  int p = 0;
+  while ((int64_t(1) << p) < x) ++p;
+  return p;
+}
+
+// ---- set-up kernels ----------------------------------------------------------
+
+__global__ void seg_classify_kernel(Params p) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= p.nseg) return;
+  const int64_t o0 = p.off[s], o1 = p.off[s + 1];
+  const bool bad = o0 < 0 || o1 < o0 || o1 > p.n || (s == 0 && o0 != 0) ||
+                   (s == p.nseg - 1 && o1 != p.n);
+  if (bad) {
+    atomicExch(&p.ctrl->status, (int)NSORT_EINVAL);
+    return;
+  }
+  const int64_t L = o1 - o0;
+  Ctrl *c = p.ctrl;
+  if (L == 0) return;
+  if (L <= p.tiny_w) {
+    p.tiny_list[atomicAdd(&c->n_tiny, 1ull)] = (int)s;
+  } else if (L <= 32 * p.small_ipt) {
+    p.small_list[atomicAdd(&c->n_small, 1ull)] = (int)s;
+  } else if (L <= p.tile) {
+    p.medium_list[atomicAdd(&c->n_medium, 1ull)] = (int)s;
+  } else {
+    const int64_t T = (L + p.tile - 1) / p.tile;
+    p.slot_base[s] = (int64_t)atomicAdd(&c->bucket_tiles[ceil_log2(T)], (unsigned long long)T);
+  }
+}
+
+// Lays out the work queue (one thread).
+__global__ void seg_plan_kernel(Params p) {
+  Ctrl *c = p.ctrl;
+  if (c->status != NSORT_OK) {
+    c->q_total = 0;
+    return;
+  }
+  unsigned long long base = 0;
+  int maxlv = 0;
+  for (int b = 0; b <= MAXLV; ++b) {
+    c->bucket_base[b] = base;
+    base += c->bucket_tiles[b];
+    if (c->bucket_tiles[b]) maxlv = b;
+  }
+  c->bucket_base[MAXLV + 1] = base;
+  c->q_medium = base;
+  c->q_small = c->q_medium + c->n_medium;
+  const unsigned long long warps = p.nt / 32;
+  c->q_tiny = c->q_small + (c->n_small + warps - 1) / warps;
+  c->q_merge = c->q_tiny + (c->n_tiny + p.nt - 1) / p.nt;
+  unsigned long long q = c->q_merge;
+  for (int k = 1; k <= maxlv; ++k) {
+    c->q_level[k] = q;
+    q += base - c->bucket_base[k];     // tiles of the segments that need k levels or more
+  }
+  c->q_level[maxlv + 1] = q;
+  c->q_total = q;
+  c->max_level = maxlv;
+}
+
+// One warp per segment: gives each large segment its global slot range and
+// records the owner of every slot.
+__global__ void seg_owner_kernel(Params p) {
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= p.nseg || p.ctrl->status != NSORT_OK) return;
+  const int64_t L = p.off[w + 1] - p.off[w];
+  if (L <= p.tile) return;
+  const int64_t T = (L + p.tile - 1) / p.tile;
+  const int64_t g = (int64_t)p.ctrl->bucket_base[ceil_log2(T)] + p.slot_base[w];
+  __syncwarp();
+  if (lane == 0) {
+    p.slot_base[w] = g;
+    p.done[w] = 0;
+  }
+  for (int64_t i = lane; i < T; i += 32) p.owner[g + i] = (int)w;
+}
+
+// ---- the persistent kernel ------------------------------------------------
+
+// Waits (thread 0 only) until *ctr >= target, for about two seconds at most;
+// on time-out records NSORT_ETIMEOUT and returns.
+__device__ void wait_at_least(unsigned long long *ctr, unsigned long long target, int *status) {
+  for (unsigned long long spins = 0;; ++spins) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(ctr) : "memory");
+    if (v >= target) return;
+    if (spins > (1ull << 24)) {
+      atomicCAS(status, (int)NSORT_OK, (int)NSORT_ETIMEOUT);
+      return;
+    }
+    __nanosleep(128);
+  }
+}
+
+// Marks one item of segment s finished: every thread fences its own
+// stores, then one thread bumps the counter.
+__device__ __forceinline__ void signal_done(unsigned long long *ctr) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) atomicAdd(ctr, 1ull);
+}
+
+template <typename K>
+__device__ __forceinline__ K make_elem(uint32_t key, int pos) {
+  if (sizeof(K) == 8) return (K)(((uint64_t)key << 32) | (uint32_t)pos);
+  return (K)key;
+}
+template <typename K>
+__device__ __forceinline__ uint32_t elem_key(K e) {
+  return sizeof(K) == 8 ? (uint32_t)((uint64_t)e >> 32) : (uint32_t)e;
+}
+template <typename K>
+__device__ __forceinline__ int elem_pos(K e) {
+  return (int)((uint64_t)e & 0xFFFFu);
+}
+
+// Tile sort with an active size m (a power of two, 512 <= m <= NT*16): only
+// the first m/16 threads hold data; all threads take part in the barriers.
+// On return thread t (< m/16) holds sorted elements [16t, 16t + 16).
+template <int NT, typename K>
+__device__ __forceinline__ void sort_tile_dyn(K (&r)[16], K *s, int m) {
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int e0 = tid * 16;
+  if (e0 < m) {   // whole warps: m is a multiple of 512
+    column_sort16(r);
+    warp_merge<16>(r, lane);
+  }
+  if (m == 512) return;
+  if (e0 < m) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) s[pidx<K>(e0 + k)] = r[k];
+  }
+  int unused[16];
+#pragma unroll 1
+  for (int run = 512; run < m; run <<= 1) {
+    __syncthreads();
+    if (e0 < m) {
+      const int g0 = e0 & ~(2 * run - 1);
+      const int diag = e0 - g0;
+      const int ai = merge_path_smem(s, g0, run, g0 + run, run, diag);
+      serial_merge<16, false>(s, g0 + ai, g0 + run, g0 + run + diag - ai, g0 + 2 * run, r, unused);
+    }
+    if (2 * run < m) {
+      __syncthreads();
+      if (e0 < m) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) s[pidx<K>(e0 + k)] = r[k];
+      }
+    }
+  }
+}
+
+// Sorts `count` elements of a segment starting at kin[base] with one CTA and
+// active size m; stores them (mapped back when `final_map`) at kdst[base].
+template <int NT, bool PAIRS>
+__device__ void block_sort_range(const Params &p, void *smem, int64_t base, int count, int m,
+                                 uint32_t *kdst, uint32_t *vdst, bool final_map) {
+  using K = typename std::conditional<PAIRS, uint64_t, uint32_t>::type;
+  K *s = static_cast<K *>(smem);
+  const int tid = threadIdx.x;
+  const int e0 = tid * 16;
+  K r[16];
+  if (e0 < m) {
+    const int act = m / 16;     // active threads; loads are striped over them
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int e = tid + act * j;
+      r[j] = e < count ? make_elem<K>(to_key(p.kin[base + e], p.dt), e) : (K)~(K)0;
+    }
+  }
+  sort_tile_dyn<NT>(r, s, m);
+  uint32_t vo[16];
+  if (PAIRS && e0 < m) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) vo[k] = e0 + k < count ? p.vin[base + elem_pos(r[k])] : 0u;
+  }
+  if (PAIRS) __syncthreads();   // every value gathered before any is overwritten in place
+  const int dto = final_map ? p.dt : (int)DT_U32;
+  if (e0 < m) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      if (e0 + k < count) {
+        kdst[base + e0 + k] = from_key(elem_key(r[k]), dto);
+        if (PAIRS) vdst[base + e0 + k] = vo[k];
+      }
+    }
+  }
+}
+
+// One warp sorts one segment of at most 32*IPT elements.
+template <int IPT, bool PAIRS>
+__device__ void warp_sort_segment(const Params &p, int64_t sid) {
+  using K = typename std::conditional<PAIRS, uint64_t, uint32_t>::type;
+  const int lane = threadIdx.x & 31;
+  const int64_t off = p.off[sid];
+  const int L = (int)(p.off[sid + 1] - off);
+  K r[IPT];
+#pragma unroll
+  for (int k = 0; k < IPT; ++k) {
+    const int e = lane + 32 * k;
+    r[k] = e < L ? make_elem<K>(to_key(p.kin[off + e], p.dt), e) : (K)~(K)0;
+  }
+  column_sort(r);
+  warp_merge<IPT>(r, lane);
+  uint32_t vo[IPT];
+  const int e0 = lane * IPT;
+  if (PAIRS) {
+#pragma unroll
+    for (int k = 0; k < IPT; ++k) vo[k] = e0 + k < L ? p.vin[off + elem_pos(r[k])] : 0u;
+    __syncwarp();
+  }
+#pragma unroll
+  for (int k = 0; k < IPT; ++k) {
+    if (e0 + k < L) {
+      p.kout[off + e0 + k] = from_key(elem_key(r[k]), p.dt);
+      if (PAIRS) p.vout[off + e0 + k] = vo[k];
+    }
+  }
+}
+
+// One thread sorts one segment of at most W elements.
+template <int W, bool PAIRS>
+__device__ void thread_sort_segment(const Params &p, int64_t sid) {
+  using K = typename std::conditional<PAIRS, uint64_t, uint32_t>::type;
+  const int64_t off = p.off[sid];
+  const int L = (int)(p.off[sid + 1] - off);
+  K r[W];
+#pragma unroll
+  for (int k = 0; k < W; ++k)
+    r[k] = k < L ? make_elem<K>(to_key(p.kin[off + k], p.dt), k) : (K)~(K)0;
+  column_sort(r);
+  uint32_t vo[W];
+  if (PAIRS) {
+#pragma unroll
+    for (int k = 0; k < W; ++k) vo[k] = k < L ? p.vin[off + elem_pos(r[k])] : 0u;
+  }
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    if (k < L) {
+      p.kout[off + k] = from_key(elem_key(r[k]), p.dt);
+      if (PAIRS) p.vout[off + k] = vo[k];
+    }
+  }
+}
+
+// Stages slices [a_off, a_off+na) and [b_off, ...) of src into s with loads
+// that see other CTAs' earlier stores (the merge levels of large segments).
+template <int NT, int VT>
+__device__ __forceinline__ void stage_slices_cg(uint32_t *s, const uint32_t *src, int64_t a_off,
+                                                int64_t b_off, int na, int count) {
+  const int tid = threadIdx.x;
+  const uint32_t *pa = src + a_off + tid;
+  const uint32_t *pb = src + b_off + (tid - na);
+  uint32_t t[VT];
+#pragma unroll
+  for (int j = 0; j < VT; ++j) {
+    const int i = tid + NT * j;
+    uint32_t v = 0;
+    if (i < na) v = __ldcg(pa + NT * j);
+    else if (i < count) v = __ldcg(pb + NT * j);
+    t[j] = v;
+  }
+  const int sbase = pidx<uint32_t>(tid);
+#pragma unroll
+  for (int j = 0; j < VT; ++j) s[sbase + j * (NT + NT / 32)] = t[j];
+}
+
+// Merge tile m of level `level` of large segment sid.
+template <int NT, bool PAIRS>
+__device__ void merge_tile(const Params &p, void *smem, int64_t *split_sh, int64_t sid, int level,
+                           int64_t m) {
+  constexpr int VT = 16;
+  constexpr int MT = NT * VT;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int64_t off = p.off[sid];
+  const int64_t L = p.off[sid + 1] - off;
+  const int64_t T = (L + p.tile - 1) / p.tile;
+  const int P = ceil_log2(T);
+  if (tid == 0) wait_at_least(&p.done[sid], (unsigned long long)level * T, &p.ctrl->status);
+  __syncthreads();
+  const bool src_tmp = ((P - level + 1) & 1) != 0;
+  const bool dst_tmp = ((P - level) & 1) != 0;
+  const uint32_t *ksrc = (src_tmp ? p.ktmp : p.kout) + off;
+  uint32_t *kdst = (dst_tmp ? p.ktmp : p.kout) + off;
+  const int64_t run = (int64_t)p.tile << (level - 1);
+  const int64_t out0 = m * MT;
+  const int64_t out1 = out0 + MT < L ? out0 + MT : L;
+  const int64_t pair0 = out0 & ~(2 * run - 1);
+  const int64_t la = L - pair0 < run ? L - pair0 : run;
+  const int64_t rest = L - pair0 - run;
+  const int64_t lb = rest <= 0 ? 0 : (rest < run ? rest : run);
+  const int64_t pair_end = pair0 + la + lb;
+  const int warp = tid >> 5;
+  if (warp == 0) {
+    const int64_t r = merge_path_global_warp<true>(ksrc + pair0, la, ksrc + pair0 + la, lb,
+                                                   out0 - pair0, lane);
+    if (lane == 0) split_sh[0] = r;
+  } else if (warp == 1) {
+    const int64_t r = out1 == pair_end ? la
+                                       : merge_path_global_warp<true>(ksrc + pair0, la,
+                                                                      ksrc + pair0 + la, lb,
+                                                                      out1 - pair0, lane);
+    if (lane == 0) split_sh[1] = r;
+  }
+  __syncthreads();
+  const int64_t a_beg = split_sh[0], a_end = split_sh[1];
+  const int na = (int)(a_end - a_beg);
+  const int count = (int)(out1 - out0);
+  const int nb = count - na;
+  const int64_t a_off = pair0 + a_beg;
+  const int64_t b_off = pair0 + la + (out0 - pair0 - a_beg);
+  uint32_t *sk = static_cast<uint32_t *>(smem);
+  uint32_t *sv = sk + merge_smem_len<uint32_t>(MT, VT);
+  stage_slices_cg<NT, VT>(sk, ksrc, a_off, b_off, na, count);
+  if (PAIRS) {
+    const uint32_t *vsrc = (src_tmp ? p.vtmp : p.vout) + off;
+    stage_slices_cg<NT, VT>(sv, vsrc, a_off, b_off, na, count);
+  }
+  __syncthreads();
+  const int diag = tid * VT < count ? tid * VT : count;
+  const int ai = merge_path_smem(sk, 0, na, na, nb, diag);
+  uint32_t o[VT];
+  int from[VT];
+  serial_merge<VT, PAIRS>(sk, ai, na, na + diag - ai, count, o, from);
+  const int dto = level == P ? p.dt : (int)DT_U32;
+  const int e0 = tid * VT;
+#pragma unroll
+  for (int k = 0; k < VT; ++k)
+    if (e0 + k < count) kdst[out0 + e0 + k] = from_key(o[k], dto);
+  if (PAIRS) {
+    uint32_t *vdst = (dst_tmp ? p.vtmp : p.vout) + off;
+#pragma unroll
+    for (int k = 0; k < VT; ++k)
+      if (e0 + k < count) vdst[out0 + e0 + k] = sv[pidx<uint32_t>(from[k])];
+  }
+  signal_done(&p.done[sid]);
+}
+
+template <int NT, bool PAIRS>
+__global__ void __launch_bounds__(NT, PAIRS ? 1 : 2) seg_sort_kernel(Params p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ unsigned long long item_sh;
+  __shared__ int64_t split_sh[2];
+  const int tid = threadIdx.x;
+  Ctrl *c = p.ctrl;
+  const unsigned long long q_medium = c->q_medium, q_small = c->q_small, q_tiny = c->q_tiny,
+                           q_merge = c->q_merge, q_total = c->q_total;
+  const int max_level = c->max_level;
+  for (;;) {
+    if (tid == 0) item_sh = atomicAdd(&c->next_item, 1ull);
+    __syncthreads();
+    const unsigned long long item = item_sh;
+    __syncthreads();
+    if (item >= q_total) break;
+    if (item < q_medium) {
+      // level 0: tile sort of one tile of a large segment
+      const int sid = p.owner[item];
+      const int64_t t = (int64_t)item - p.slot_base[sid];
+      const int64_t off = p.off[sid];
+      const int64_t L = p.off[sid + 1] - off;
+      const int P = ceil_log2((L + p.tile - 1) / p.tile);
+      const int64_t b0 = t * p.tile;
+      const int count = (int)(L - b0 < p.tile ? L - b0 : p.tile);
+      uint32_t *kd = (P & 1) ? p.ktmp : p.kout;
+      uint32_t *vd = (P & 1) ? p.vtmp : p.vout;
+      block_sort_range<NT, PAIRS>(p, smem_raw, off + b0, count, NT * 16, kd, vd, false);
+      signal_done(&p.done[sid]);
+    } else if (item < q_small) {
+      const int sid = p.medium_list[item - q_medium];
+      const int64_t off = p.off[sid];
+      const int L = (int)(p.off[sid + 1] - off);
+      int m = 512;
+      while (m < L) m <<= 1;
+      block_sort_range<NT, PAIRS>(p, smem_raw, off, L, m, p.kout, p.vout, true);
+    } else if (item < q_tiny) {
+      const unsigned long long idx = (item - q_small) * (NT / 32) + (tid >> 5);
+      if (idx < c->n_small) {
+        const int sid = p.small_list[idx];
+        if (p.small_ipt == 8) warp_sort_segment<8, PAIRS>(p, sid);
+        else warp_sort_segment<16, PAIRS>(p, sid);
+      }
+    } else if (item < q_merge) {
+      const unsigned long long idx = (item - q_tiny) * NT + tid;
+      if (idx < c->n_tiny) {
+        const int sid = p.tiny_list[idx];
+        if (p.tiny_w == 8) thread_sort_segment<8, PAIRS>(p, sid);
+        else thread_sort_segment<16, PAIRS>(p, sid);
+      }
+    } else {
+      int k = 1;
+      while (k < max_level && item >= c->q_level[k + 1]) ++k;
+      const unsigned long long slot = c->bucket_base[k] + (item - c->q_level[k]);
+      const int sid = p.owner[slot];
+      merge_tile<NT, PAIRS>(p, smem_raw, split_sh, sid, k, (int64_t)slot - p.slot_base[sid]);
+    }
+  }
+}
+
+// ---- host side -------------------------------------------------------------
+
+struct Layout {
+  size_t ctrl, keys, vals, tiny, small, medium, slot, done, owner, total;
+};
+
+Layout layout(uint64_t n, uint64_t nseg, bool pairs) {
+  Layout l{};
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o = align_up(o + bytes, 256);
+    return at;
+  };
+  l.ctrl = take(sizeof(Ctrl));
+  l.keys = take(n * 4);
+  l.vals = pairs ? take(n * 4) : 0;
+  l.tiny = take(nseg * 4);
+  l.small = take(nseg * 4);
+  l.medium = take(nseg * 4);
+  l.slot = take(nseg * 8);
+  l.done = take(nseg * 8);
+  l.owner = take((2 * (n / MIN_TILE) + 2) * 4);
+  l.total = o;
+  return l;
+}
+
+std::mutex g_cfg_mu;
+nsort_seg_config g_cfg = {512, 16, 16, 0};
+
+template <int NT, bool PAIRS>
+size_t smem_bytes() {
+  using K = typename std::conditional<PAIRS, uint64_t, uint32_t>::type;
+  const size_t tile_b = sizeof(K) * merge_smem_len<K>(NT * 16, 16);
+  const size_t merge_b = sizeof(uint32_t) * 2 * merge_smem_len<uint32_t>(NT * 16, 16);
+  return tile_b > merge_b ? tile_b : merge_b;
+}
+
+template <int NT, bool PAIRS>
+int launch_sort(const Params &p, int blocks_per_sm, cudaStream_t st) {
+  const size_t smem = smem_bytes<NT, PAIRS>();
+  int dev = 0, sms = 0, occ = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaFuncSetAttribute(seg_sort_kernel<NT, PAIRS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, seg_sort_kernel<NT, PAIRS>, NT, smem) !=
+          cudaSuccess) {
+    set_last_error(std::string("nsort_segmented set-up: ") + cudaGetErrorString(cudaGetLastError()));
+    return NSORT_ECUDA;
+  }
+  if (occ < 1) occ = 1;
+  const int per_sm = blocks_per_sm > 0 && blocks_per_sm < occ ? blocks_per_sm : occ;
+  TraceScope tr(TK_SEG_SORT, st);
+  seg_sort_kernel<NT, PAIRS><<<sms * per_sm, NT, smem, st>>>(p);
+  return NSORT_OK;
+}
+
+}  // namespace seg
+
+size_t segmented_temp_bytes(int kind, uint64_t n, uint64_t nseg) {
+  if (kind != NSORT_KIND_SEGMENTED && kind != NSORT_KIND_SEGMENTED_PAIRS) return 0;
+  return seg::layout(n, nseg, kind == NSORT_KIND_SEGMENTED_PAIRS).total;
+}
+
+}  // namespace nsort
+
+using namespace nsort;
+
+extern "C" int nsort_segmented_set_config(const nsort_seg_config *cfg) {
+  if (!cfg) return NSORT_EINVAL;
+  if ((cfg->block_threads != 256 && cfg->block_threads != 512) ||
+      (cfg->tiny_width != 8 && cfg->tiny_width != 16) ||
+      (cfg->small_ipt != 8 && cfg->small_ipt != 16) || cfg->blocks_per_sm < 0)
+    return NSORT_EINVAL;
+  std::lock_guard<std::mutex> lk(seg::g_cfg_mu);
+  seg::g_cfg = *cfg;
+  return NSORT_OK;
+}
+
+extern "C" int nsort_segmented_get_config(nsort_seg_config *cfg) {
+  if (!cfg) return NSORT_EINVAL;
+  std::lock_guard<std::mutex> lk(seg::g_cfg_mu);
+  *cfg = seg::g_cfg;
+  return NSORT_OK;
+}
+
+extern "C" int nsort_segmented(const void *d_keys_in, void *d_keys_out, const uint32_t *d_vals_in,
+                               uint32_t *d_vals_out, const int64_t *d_offsets, uint64_t nseg,
+                               uint64_t n, int dtype, void *d_tmp, size_t tmp_bytes,
+                               void *stream) {
+  if (dtype != NSORT_U32 && dtype != NSORT_I32 && dtype != NSORT_F32) return NSORT_EINVAL;
+  if (n > MAX_KEYS || nseg >= (uint64_t(1) << 31)) return NSORT_EINVAL;
+  if ((d_vals_in == nullptr) != (d_vals_out == nullptr)) return NSORT_EINVAL;
+  if (nseg == 0) return n == 0 ? NSORT_OK : NSORT_EINVAL;
+  if (!d_offsets || (n > 0 && (!d_keys_in || !d_keys_out))) return NSORT_EINVAL;
+  const uintptr_t al = reinterpret_cast<uintptr_t>(d_keys_in) |
+                       reinterpret_cast<uintptr_t>(d_keys_out) |
+                       reinterpret_cast<uintptr_t>(d_vals_in) |
+                       reinterpret_cast<uintptr_t>(d_vals_out);
+  if ((al & 3) || (reinterpret_cast<uintptr_t>(d_offsets) & 7)) return NSORT_EINVAL;
+  const bool pairs = d_vals_in != nullptr;
+  const seg::Layout l = seg::layout(n, nseg, pairs);
+  if (!d_tmp || tmp_bytes < l.total) return NSORT_ENOMEM;
+  if (reinterpret_cast<uintptr_t>(d_tmp) & 255) return NSORT_EINVAL;
+  nsort_seg_config cfg;
+  {
+    std::lock_guard<std::mutex> lk(seg::g_cfg_mu);
+    cfg = seg::g_cfg;
+  }
+  char *t = static_cast<char *>(d_tmp);
+  seg::Params p;
+  p.kin = static_cast<const uint32_t *>(d_keys_in);
+  p.kout = static_cast<uint32_t *>(d_keys_out);
+  p.vin = d_vals_in;
+  p.vout = d_vals_out;
+  p.ktmp = reinterpret_cast<uint32_t *>(t + l.keys);
+  p.vtmp = pairs ? reinterpret_cast<uint32_t *>(t + l.vals) : nullptr;
+  p.off = d_offsets;
+  p.nseg = (int64_t)nseg;
+  p.n = (int64_t)n;
+  p.ctrl = reinterpret_cast<seg::Ctrl *>(t + l.ctrl);
+  p.tiny_list = reinterpret_cast<int *>(t + l.tiny);
+  p.small_list = reinterpret_cast<int *>(t + l.small);
+  p.medium_list = reinterpret_cast<int *>(t + l.medium);
+  p.slot_base = reinterpret_cast<int64_t *>(t + l.slot);
+  p.done = reinterpret_cast<unsigned long long *>(t + l.done);
+  p.owner = reinterpret_cast<int *>(t + l.owner);
+  p.dt = dtype;
+  p.nt = cfg.block_threads;
+  p.tile = cfg.block_threads * 16;
+  p.tiny_w = cfg.tiny_width;
+  p.small_ipt = cfg.small_ipt;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(p.ctrl, 0, sizeof(seg::Ctrl), st) != cudaSuccess) {
+    set_last_error(std::string("nsort_segmented: ") + cudaGetErrorString(cudaGetLastError()));
+    return NSORT_ECUDA;
+  }
+  const unsigned cblocks = (unsigned)((nseg + 255) / 256);
+  {
+    TraceScope tr(TK_SEG_BIN, st);
+    seg::seg_classify_kernel<<<cblocks, 256, 0, st>>>(p);
+    seg::seg_plan_kernel<<<1, 1, 0, st>>>(p);
+    seg::seg_owner_kernel<<<(unsigned)((nseg * 32 + 255) / 256), 256, 0, st>>>(p);
+  }
+  int rc;
+  if (p.nt == 512) rc = pairs ? seg::launch_sort<512, true>(p, cfg.blocks_per_sm, st)
+                              : seg::launch_sort<512, false>(p, cfg.blocks_per_sm, st);
+  else rc = pairs ? seg::launch_sort<256, true>(p, cfg.blocks_per_sm, st)
+                  : seg::launch_sort<256, false>(p, cfg.blocks_per_sm, st);
+  if (rc != NSORT_OK) return rc;
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_last_error(std::string("nsort_segmented: ") + cudaGetErrorString(e));
+    return NSORT_ECUDA;
+  }
+  return NSORT_OK;
+}
+
+extern "C" int nsort_segmented_status(const void *d_tmp, void *stream) {
+  if (!d_tmp) return NSORT_EINVAL;
+  int status = 0;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (cudaMemcpyAsync(&status, d_tmp, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    set_last_error(std::string("nsort_segmented_status: ") +
+                   cudaGetErrorString(cudaGetLastError()));
+    return NSORT_ECUDA;
+  }
+  return status;
+}

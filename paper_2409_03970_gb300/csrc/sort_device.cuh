@@ -53,6 +53,13 @@ template <typename K>
 __device__ __forceinline__ int pidx(int e) { return e + (e >> Pad<K>::SHIFT); }
 template <typename K>
 __host__ __device__ constexpr int padded_len(int tile) { return tile + (tile >> Pad<K>::SHIFT) + 2; }
+// Shared-memory length for a tile that serial merges of VT outputs read
+// without clamping their indices: they may look up to VT + 1 elements past
+// the end of the tile.
+template <typename K>
+__host__ __device__ constexpr int merge_smem_len(int tile, int vt) {
+  return padded_len<K>(tile + vt + 2);
+}
 
 // ---- compare-exchange --------------------------------------------------
 __device__ __forceinline__ uint32_t kmin(uint32_t a, uint32_t b) { return a < b ? a : b; }
@@ -102,46 +109,69 @@ __device__ __forceinline__ K keep(bool lower, K mine, K other) {
   return lower ? kmin(mine, other) : kmax(mine, other);
 }
 
-// In-thread half-cleaners at distances 8, 4, 2, 1: sorts each thread's 16
-// registers once they form a bitonic sequence (the serial tail).
+// 8-input network for 8 keys per thread: Batcher's odd-even merge sort,
+// 19 comparators in 6 layers, which is also the fewest possible for n = 8
+// (Table 1, n = 8).
 template <typename K>
-__device__ __forceinline__ void thread_tail16(K (&r)[16]) {
+__device__ __forceinline__ void column_sort8(K (&r)[8]) {
+  ce(r[0], r[1]); ce(r[2], r[3]); ce(r[4], r[5]); ce(r[6], r[7]);
+  ce(r[0], r[2]); ce(r[1], r[3]); ce(r[4], r[6]); ce(r[5], r[7]);
+  ce(r[1], r[2]); ce(r[5], r[6]);
+  ce(r[0], r[4]); ce(r[1], r[5]); ce(r[2], r[6]); ce(r[3], r[7]);
+  ce(r[2], r[4]); ce(r[3], r[5]);
+  ce(r[1], r[2]); ce(r[3], r[4]); ce(r[5], r[6]);
+}
+
+template <typename K>
+__device__ __forceinline__ void column_sort(K (&r)[16]) { column_sort16(r); }
+template <typename K>
+__device__ __forceinline__ void column_sort(K (&r)[8]) { column_sort8(r); }
+
+// In-thread half-cleaners at distances IPT/2, ..., 1: sorts each thread's
+// IPT registers once they form a bitonic sequence (the serial tail).
+template <int IPT, typename K>
+__device__ __forceinline__ void thread_tail(K (&r)[IPT]) {
 #pragma unroll
-  for (int d = 8; d >= 1; d >>= 1) {
+  for (int d = IPT / 2; d >= 1; d >>= 1) {
 #pragma unroll
-    for (int i = 0; i < 16; ++i)
+    for (int i = 0; i < IPT; ++i)
       if (!(i & d)) ce(r[i], r[i + d]);
   }
 }
 
-// Lane l holds a sorted run of 16 in r[0..15] (warp element 16*l + k).
-// Merges the 32 runs into one sorted run of 512 in five levels.  Level j
-// merges groups of 2^(j-1) lanes pairwise: a flip stage (element p against
-// element 2m-1-p of the 2m-element group: lane l ^ (2^j - 1), register
-// 15 - k), half-cleaner stages across lanes at lane distances 2^(j-2)..1,
-// then the in-thread tail.  In each cross-lane comparator the lower lane
-// keeps the minimum and the upper lane the maximum.
-template <typename K>
-__device__ __forceinline__ void warp_merge512(K (&r)[16], int lane) {
+// Lane l holds a sorted run of IPT in r[] (warp element IPT*l + k).  Merges
+// the 32 runs into one sorted run of 32*IPT in five levels.  Level j merges
+// groups of 2^(j-1) lanes pairwise: a flip stage (element p against element
+// 2m-1-p of the 2m-element group: lane l ^ (2^j - 1), register IPT-1-k),
+// half-cleaner stages across lanes at lane distances 2^(j-2)..1, then the
+// in-thread tail.  In each cross-lane comparator the lower lane keeps the
+// minimum and the upper lane the maximum.
+template <int IPT, typename K>
+__device__ __forceinline__ void warp_merge(K (&r)[IPT], int lane) {
 #pragma unroll
   for (int j = 1; j <= 5; ++j) {
     const int span = 1 << j;
     const bool lower = !(lane & (span >> 1));
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const K from_hi = shfl_x(r[15 - k], span - 1);   // partner's mirror of r[k]
-      const K from_lo = shfl_x(r[k], span - 1);        // partner's mirror of r[15-k]
+    for (int k = 0; k < IPT / 2; ++k) {
+      const K from_hi = shfl_x(r[IPT - 1 - k], span - 1);   // partner's mirror of r[k]
+      const K from_lo = shfl_x(r[k], span - 1);             // partner's mirror of r[IPT-1-k]
       r[k] = keep(lower, r[k], from_hi);
-      r[15 - k] = keep(lower, r[15 - k], from_lo);
+      r[IPT - 1 - k] = keep(lower, r[IPT - 1 - k], from_lo);
     }
 #pragma unroll
     for (int d = span >> 2; d >= 1; d >>= 1) {
       const bool lo2 = !(lane & d);
 #pragma unroll
-      for (int k = 0; k < 16; ++k) r[k] = keep(lo2, r[k], shfl_x(r[k], d));
+      for (int k = 0; k < IPT; ++k) r[k] = keep(lo2, r[k], shfl_x(r[k], d));
     }
-    thread_tail16(r);
+    thread_tail<IPT>(r);
   }
+}
+
+template <typename K>
+__device__ __forceinline__ void warp_merge512(K (&r)[16], int lane) {
+  warp_merge<16>(r, lane);
 }
 
 // ---- merge path (Sec. 2.1: load-balanced partitioning) -------------------
@@ -161,7 +191,7 @@ __device__ __forceinline__ int merge_path_smem(const K *s, int a0, int na, int b
   return lo;
 }
 
-// Same search on global memory (64-bit lengths).
+// Same search on global memory, one thread (64-bit lengths).
 __device__ __forceinline__ int64_t merge_path_global(const uint32_t *A, int64_t na,
                                                      const uint32_t *B, int64_t nb,
                                                      int64_t diag) {
@@ -169,8 +199,43 @@ __device__ __forceinline__ int64_t merge_path_global(const uint32_t *A, int64_t 
   int64_t hi = diag < na ? diag : na;
   while (lo < hi) {
     const int64_t mid = (lo + hi) >> 1;
-    if (A[mid] <= B[diag - 1 - mid]) lo = mid + 1;
+    if (__ldg(A + mid) <= __ldg(B + (diag - 1 - mid))) lo = mid + 1;
     else hi = mid;
+  }
+  return lo;
+}
+
+// Same search on global memory, by a whole warp: each round the 32 lanes
+// test 32 evenly spaced candidates at once, which shrinks the interval by a
+// factor of about 33 (6 rounds of loads for a 2^27-long run instead of 27
+// dependent loads).  All lanes must call it with the same arguments; all get
+// the result.
+// COHERENT loads bypass L1 (ld.global.cg), for data written earlier in the
+// same launch by other CTAs; otherwise the read-only path is used.
+template <bool COHERENT>
+__device__ __forceinline__ uint32_t load_key(const uint32_t *p) {
+  return COHERENT ? __ldcg(p) : __ldg(p);
+}
+
+template <bool COHERENT = false>
+__device__ __forceinline__ int64_t merge_path_global_warp(const uint32_t *A, int64_t na,
+                                                          const uint32_t *B, int64_t nb,
+                                                          int64_t diag, int lane) {
+  int64_t lo = diag - nb > 0 ? diag - nb : 0;
+  int64_t hi = diag < na ? diag : na;
+  while (lo < hi) {                                  // answer in [lo, hi]
+    const int64_t step = (hi - lo + 32) / 33;        // >= 1
+    const int64_t q = lo + (int64_t)(lane + 1) * step - 1;
+    bool p = false;                                  // p: A[q] goes before the diagonal
+    if (q < hi) p = load_key<COHERENT>(A + q) <= load_key<COHERENT>(B + (diag - 1 - q));
+    const int c = __popc(__ballot_sync(0xffffffffu, p));   // true probes form a prefix
+    int64_t nhi = hi;
+    if (c < 32) {
+      const int64_t qc = lo + (int64_t)(c + 1) * step - 1;
+      if (qc < hi) nhi = qc;
+    }
+    lo = lo + (int64_t)c * step;
+    hi = nhi;
   }
   return lo;
 }
@@ -178,24 +243,22 @@ __device__ __forceinline__ int64_t merge_path_global(const uint32_t *A, int64_t 
 // ---- serial merge (the serial half of the hybrid merger) ----------------
 // Produces VT outputs of the stable merge of s[a, a_end) and s[b, b_end)
 // (element indices, padded layout) into out[].  Branch-free: one compare,
-// selects and one shared load per output.  Indices are clamped to `limit`
-// (the last readable element) so that a thread whose range runs past the
-// end of both runs never reads outside the buffer; such outputs are
-// discarded by the caller.  src[k] receives the element index each output
-// came from when TRACK is set.
+// selects and one shared load per output.  A thread whose range runs past
+// the end of both runs keeps going (its extra outputs are discarded by the
+// caller); it then reads at most VT + 1 elements past the larger end, which
+// the buffer must hold (merge_smem_len).  src[k] receives the element index
+// each output came from when TRACK is set.
 template <int VT, bool TRACK, typename K>
 __device__ __forceinline__ void serial_merge(const K *s, int a, int a_end, int b, int b_end,
-                                             int limit, K (&out)[VT], int (&src)[VT]) {
-  K ka = s[pidx<K>(a < limit ? a : limit)];
-  K kb = s[pidx<K>(b < limit ? b : limit)];
+                                             K (&out)[VT], int (&src)[VT]) {
+  K ka = s[pidx<K>(a)];
+  K kb = s[pidx<K>(b)];
 #pragma unroll
   for (int k = 0; k < VT; ++k) {
     const bool take_a = (b >= b_end) || (a < a_end && ka <= kb);
     out[k] = take_a ? ka : kb;
     if (TRACK) src[k] = take_a ? a : b;
-    int nxt = (take_a ? a : b) + 1;
-    nxt = nxt < limit ? nxt : limit;
-    const K kn = s[pidx<K>(nxt)];
+    const K kn = s[pidx<K>((take_a ? a : b) + 1)];
     ka = take_a ? kn : ka;
     kb = take_a ? kb : kn;
     a += take_a;

@@ -26,6 +26,15 @@ _lock = threading.Lock()
 _lib = None
 
 
+class SegConfig(ctypes.Structure):
+    """nsort_seg_config: tunables of the segmented sort."""
+    _fields_ = [("block_threads", ctypes.c_int), ("tiny_width", ctypes.c_int),
+                ("small_ipt", ctypes.c_int), ("blocks_per_sm", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class NsortError(RuntimeError):
     def __init__(self, status: int, what: str):
         lib = _load()
@@ -55,6 +64,14 @@ def _load():
         lib.nsort_keys.restype = i32
         lib.nsort_pairs.argtypes = [vp, vp, vp, vp, u64, i32, vp, sz, vp]
         lib.nsort_pairs.restype = i32
+        lib.nsort_segmented.argtypes = [vp, vp, vp, vp, vp, u64, u64, i32, vp, sz, vp]
+        lib.nsort_segmented.restype = i32
+        lib.nsort_segmented_status.argtypes = [vp, vp]
+        lib.nsort_segmented_status.restype = i32
+        lib.nsort_segmented_set_config.argtypes = [ctypes.POINTER(SegConfig)]
+        lib.nsort_segmented_set_config.restype = i32
+        lib.nsort_segmented_get_config.argtypes = [ctypes.POINTER(SegConfig)]
+        lib.nsort_segmented_get_config.restype = i32
         lib.nsort_keys_noalloc.argtypes = [vp, vp, u64, i32, vp]
         lib.nsort_keys_noalloc.restype = i32
         lib.nsort_trace_enable.argtypes = [i32]
@@ -135,6 +152,31 @@ def nsort_pairs(keys_in, vals_in, keys_out, vals_out, n: int, dtype: int, tmp, t
                                dtype, _ptr(tmp), tmp_bytes, _stream(stream))
 
 
+def nsort_segmented(keys_in, keys_out, vals_in, vals_out, offsets, nseg: int, n: int,
+                    dtype: int, tmp, tmp_bytes: int, stream=None) -> int:
+    return _load().nsort_segmented(_ptr(keys_in), _ptr(keys_out), _ptr(vals_in), _ptr(vals_out),
+                                   _ptr(offsets), nseg, n, dtype, _ptr(tmp), tmp_bytes,
+                                   _stream(stream))
+
+
+def nsort_segmented_status(tmp, stream=None) -> int:
+    return _load().nsort_segmented_status(_ptr(tmp), _stream(stream))
+
+
+def nsort_segmented_set_config(block_threads=512, tiny_width=16, small_ipt=16,
+                               blocks_per_sm=0) -> int:
+    cfg = SegConfig(block_threads, tiny_width, small_ipt, blocks_per_sm)
+    return _load().nsort_segmented_set_config(ctypes.byref(cfg))
+
+
+def nsort_segmented_get_config() -> dict:
+    cfg = SegConfig()
+    rc = _load().nsort_segmented_get_config(ctypes.byref(cfg))
+    if rc != OK:
+        raise NsortError(rc, "nsort_segmented_get_config")
+    return cfg.as_dict()
+
+
 NOALLOC_MAX_KEYS = 1 << 20
 
 
@@ -192,6 +234,35 @@ def sort(keys, out=None, tmp=None, stream=None):
     if rc != OK:
         raise NsortError(rc, "nsort_keys")
     return out
+
+
+def sort_segmented(keys, offsets, vals=None, keys_out=None, vals_out=None, tmp=None,
+                   stream=None, check=True):
+    """Sorts each segment [offsets[s], offsets[s+1]) of a 1-D CUDA key tensor
+    on its own (stable with values).  offsets: int64 CUDA tensor of nseg+1
+    entries.  check=True synchronises and raises on a device-side error
+    (malformed offsets)."""
+    import torch
+    _check_1d(keys, "keys")
+    if offsets.dtype != torch.int64 or not offsets.is_cuda or offsets.dim() != 1:
+        raise ValueError("offsets must be a 1-D int64 CUDA tensor")
+    dt = dtype_code(keys)
+    n, nseg = keys.numel(), offsets.numel() - 1
+    keys_out = torch.empty_like(keys) if keys_out is None else keys_out
+    if vals is not None:
+        vals_out = torch.empty_like(vals) if vals_out is None else vals_out
+    kind = KIND_SEGMENTED if vals is None else KIND_SEGMENTED_PAIRS
+    if tmp is None:
+        tmp = scratch(kind, n, nseg, device=keys.device)
+    rc = nsort_segmented(keys, keys_out, vals, vals_out, offsets, nseg, n, dt, tmp, tmp.numel(),
+                         stream)
+    if rc != OK:
+        raise NsortError(rc, "nsort_segmented")
+    if check:
+        st = nsort_segmented_status(tmp, stream)
+        if st != OK:
+            raise NsortError(st, "nsort_segmented (device status)")
+    return keys_out if vals is None else (keys_out, vals_out)
 
 
 def sort_pairs(keys, vals, keys_out=None, vals_out=None, tmp=None, stream=None):
