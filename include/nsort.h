@@ -111,19 +111,13 @@ int nsort_pairs(const void *d_keys_in, const uint32_t *d_vals_in,
  * nsort_temp_bytes(NSORT_KIND_SEGMENTED[_PAIRS], n, nseg, dtype), 256-byte
  * aligned; in-place (in == out) is allowed.  Host-checked errors:
  * NSORT_EINVAL, NSORT_ENOMEM, NSORT_ECUDA.  Malformed offsets are found on
- * the device: the batch is left unsorted and nsort_segmented_status()
+ * the device: the batch is left unsorted and nsort_device_status()
  * reports NSORT_EINVAL.  Source: the paper's sort (Sec. 2.1) applied per
  * segment; the batching is this library's extension. */
 int nsort_segmented(const void *d_keys_in, void *d_keys_out,
                     const uint32_t *d_vals_in, uint32_t *d_vals_out,
                     const int64_t *d_offsets, uint64_t nseg, uint64_t n, int dtype,
                     void *d_tmp, size_t tmp_bytes, void *stream);
-
-/* Synchronises `stream` and returns the device-side status of the last
- * nsort_segmented call that used d_tmp: NSORT_OK, NSORT_EINVAL (malformed
- * offsets) or NSORT_ETIMEOUT (a merge level waited too long for its inputs;
- * the result is then incomplete). */
-int nsort_segmented_status(const void *d_tmp, void *stream);
 
 /* Tunables of nsort_segmented, set by the autotuner (process-wide). */
 typedef struct {
@@ -174,6 +168,15 @@ int nsort_trace_enable(int on);
 /* Waits for the recorded events, writes one entry per kernel name (at most
  * `capacity`; *count = number of names seen) and drops the records. */
 int nsort_trace_read(nsort_trace_entry *out, int capacity, int *count);
+
+/* Synchronises `stream` and returns the device-side status word of the last
+ * call that used the scratch buffer d_tmp (the first 4 bytes of every
+ * scratch layout): NSORT_OK; NSORT_EINVAL (nsort_segmented: malformed
+ * offsets); NSORT_ETIMEOUT (a bounded wait inside a kernel gave up — the
+ * output of that call is then incomplete; this does not happen in normal
+ * operation).  Calls that need no scratch (n within one tile) have no
+ * status word. */
+int nsort_device_status(const void *d_tmp, void *stream);
 
 /* Human-readable text of an nsort_status. */
 const char *nsort_status_string(int status);

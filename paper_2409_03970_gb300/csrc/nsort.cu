@@ -24,6 +24,7 @@
 #include "nsort.h"
 #include "nsort_internal.h"
 #include "sort_device.cuh"
+#include "tma_device.cuh"
 
 namespace nsort {
 
@@ -292,6 +293,183 @@ __global__ void __launch_bounds__(NT, 3) merge_pairs_kernel(const uint32_t *__re
   store_run<VT, DT_U32>(ov, vo, g.count, full);
 }
 
+// ---- persistent merge pass with bulk copies (TMA) ------------------------
+//
+// Tiles are laid out per run pair: pair p (A = run 2p, B = run 2p+1) owns
+// tiles_per_pair = ceil(2*run / TILE) consecutive tiles, so no tile spans
+// two pairs and TILE need not be a power of two.  TILE = NT * VT with VT
+// odd: thread t starts its merge near element VT*t/2 of each run, which
+// spreads a warp's shared-memory reads over the banks without padding (so
+// the slices can be staged by plain 1-D bulk copies).
+
+struct PairTile {
+  int64_t out0;    // first output of the tile
+  int64_t a_off;   // global index of the A slice
+  int64_t b_off;   // global index of the B slice
+  int na, nb, count;
+};
+
+__device__ __forceinline__ PairTile pair_tile(int64_t t, int64_t n, int64_t run, int64_t tpp,
+                                              int tile, const int64_t *split) {
+  PairTile g;
+  const int64_t pair = t / tpp;
+  const int64_t j = t - pair * tpp;
+  const int64_t pair0 = pair * 2 * run;
+  const int64_t la = n - pair0 < run ? n - pair0 : run;
+  const int64_t rest = n - pair0 - run;
+  const int64_t lb = rest <= 0 ? 0 : (rest < run ? rest : run);
+  const int64_t pend = pair0 + la + lb;
+  g.out0 = pair0 + j * tile;
+  const int64_t out1 = g.out0 + tile < pend ? g.out0 + tile : pend;
+  const int64_t a_beg = split[t];
+  const int64_t a_end = out1 == pend ? la : split[t + 1];
+  g.a_off = pair0 + a_beg;
+  g.b_off = pair0 + la + (g.out0 - pair0 - a_beg);
+  g.na = (int)(a_end - a_beg);
+  g.count = (int)(out1 - g.out0);
+  g.nb = g.count - g.na;
+  return g;
+}
+
+// Splitters for the pair-aligned tiling, one thread per tile.
+__global__ void partition_pairs_kernel(const uint32_t *__restrict__ src, int64_t n, int64_t run,
+                                       int64_t tpp, int tile, int64_t num_tiles,
+                                       int64_t *__restrict__ split) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= num_tiles) return;
+  const int64_t pair = t / tpp;
+  const int64_t j = t - pair * tpp;
+  const int64_t pair0 = pair * 2 * run;
+  const int64_t la = n - pair0 < run ? n - pair0 : run;
+  const int64_t rest = n - pair0 - run;
+  const int64_t lb = rest <= 0 ? 0 : (rest < run ? rest : run);
+  split[t] = merge_path_global(src + pair0, la, src + pair0 + la, lb, j * tile);
+}
+
+// Where a tile's slices sit in its shared-memory buffer.  The A window
+// starts at the 16-byte boundary below a_off, so A[i] is at sh_a + i; the B
+// window starts at the next 16-byte boundary after A.
+struct SmemSlices {
+  int sh_a, base_b, sh_b;
+};
+__device__ __forceinline__ SmemSlices smem_slices(const PairTile &g) {
+  SmemSlices l;
+  l.sh_a = (int)(g.a_off & 3);
+  l.base_b = (l.sh_a + g.na + 3) & ~3;
+  l.sh_b = (int)(g.b_off & 3);
+  return l;
+}
+
+// Issues the bulk copies of tile g's slices into buf (thread 0 only).  The
+// windows are rounded to 16 bytes and clipped at n_al = n & ~3; elements
+// beyond n_al (at most 3 per slice, only at the very end of the array) are
+// loaded separately with ordinary loads.
+__device__ __forceinline__ void issue_tile_loads(const uint32_t *src, int64_t n_al,
+                                                 const PairTile &g, uint32_t *buf, uint64_t *bar) {
+  const SmemSlices l = smem_slices(g);
+  int64_t a0 = g.a_off & ~int64_t(3), a1 = (g.a_off + g.na + 3) & ~int64_t(3);
+  int64_t b0 = g.b_off & ~int64_t(3), b1 = (g.b_off + g.nb + 3) & ~int64_t(3);
+  if (a1 > n_al) a1 = n_al;
+  if (b1 > n_al) b1 = n_al;
+  const uint32_t bytes_a = (g.na > 0 && a1 > a0) ? (uint32_t)((a1 - a0) * 4) : 0u;
+  const uint32_t bytes_b = (g.nb > 0 && b1 > b0) ? (uint32_t)((b1 - b0) * 4) : 0u;
+  mbar_arrive_expect_tx(bar, bytes_a + bytes_b);
+  if (bytes_a) bulk_load(buf, src + a0, bytes_a, bar);
+  if (bytes_b) bulk_load(buf + l.base_b, src + b0, bytes_b, bar);
+}
+
+// Per tile, one CTA-wide barrier: after it, every thread is done with the
+// previous tile, so thread 0 can reuse that buffer for the next tile's
+// copies while the CTA merges this one.  Each warp's outputs are contiguous
+// (32 * VT keys), so each warp stages and bulk-stores its own part with
+// warp-level synchronisation only.
+template <int NT, int VT, int DT_OUT>
+__global__ void __launch_bounds__(NT, 4) merge_keys_tma_kernel(
+    const uint32_t *__restrict__ src, uint32_t *__restrict__ dst, int64_t n, int64_t run,
+    int64_t tpp, int64_t num_tiles, const int64_t *__restrict__ split, int *status) {
+  constexpr int TILE = NT * VT;
+  constexpr int WOUT = 32 * VT;                       // outputs per warp
+  constexpr int IN_LEN = (TILE + 12 + VT + 2 + 3) & ~3;
+  static_assert(WOUT % 4 == 0, "warp output slices must be 16-byte multiples");
+  __shared__ __align__(128) uint32_t in_buf[2][IN_LEN];
+  __shared__ __align__(128) uint32_t out_buf[TILE];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ PairTile desc[2];   // geometry of the tile in each buffer, written by thread 0
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
+  const int64_t n_al = n & ~int64_t(3);
+  int64_t t = blockIdx.x;
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+    if (t < num_tiles) {
+      desc[0] = pair_tile(t, n, run, tpp, TILE, split);
+      issue_tile_loads(src, n_al, desc[0], in_buf[0], &bar[0]);
+    }
+  }
+  __syncthreads();
+  bool ok = true;
+  uint32_t *wout = out_buf + warp * WOUT;
+  for (int it = 0; t < num_tiles; ++it, t += gridDim.x) {
+    const int b = it & 1;
+    const int64_t tn = t + gridDim.x;
+    const uint32_t parity = (uint32_t)((it >> 1) & 1);
+    const bool got = mbar_wait(&bar[b], parity);
+    if (!__syncthreads_and(got)) {
+      // a copy did not arrive in time: wait (bounded) for the copies still
+      // in flight into this CTA's shared memory, report, and stop
+      if (tid == 0) mbar_wait(&bar[b], parity);
+      ok = false;
+      break;
+    }
+    // all threads are past the previous tile: its buffer and descriptor are free
+    if (tid == 0 && tn < num_tiles) {
+      desc[b ^ 1] = pair_tile(tn, n, run, tpp, TILE, split);
+      issue_tile_loads(src, n_al, desc[b ^ 1], in_buf[b ^ 1], &bar[b ^ 1]);
+    }
+    const PairTile g = desc[b];
+    const SmemSlices l = smem_slices(g);
+    uint32_t *s = in_buf[b];
+    if (g.a_off + g.na > n_al || g.b_off + g.nb > n_al) {   // uniform: the array's last tile
+      if (tid < 4) {
+        const int64_t ia = (g.a_off > n_al ? g.a_off : n_al) + tid;
+        if (ia < g.a_off + g.na) s[l.sh_a + (int)(ia - g.a_off)] = src[ia];
+        const int64_t ib = (g.b_off > n_al ? g.b_off : n_al) + tid;
+        if (ib < g.b_off + g.nb) s[l.base_b + l.sh_b + (int)(ib - g.b_off)] = src[ib];
+        fence_proxy_async_smem();   // ordered before later bulk copies into this buffer
+      }
+      __syncthreads();
+    }
+    const int a0 = l.sh_a, b0 = l.base_b + l.sh_b;
+    const int diag = tid * VT < g.count ? tid * VT : g.count;
+    const int ai = merge_path_plain(s, a0, g.na, b0, g.nb, diag);
+    uint32_t o[VT];
+    serial_merge_plain<VT>(s, a0 + ai, a0 + g.na, b0 + diag - ai, b0 + g.nb, o);
+    // this warp's slice of the output: stage, then one bulk store by lane 0
+    const int w0 = warp * WOUT;
+    const int wcount = g.count - w0 < WOUT ? g.count - w0 : WOUT;
+    if (lane == 0) bulk_wait_read_all();   // the warp's previous store has left wout
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < VT; ++k)
+      if (tid * VT + k < g.count) wout[lane * VT + k] = from_key(o[k], DT_OUT);
+    fence_proxy_async_smem();
+    __syncwarp();
+    if (wcount > 0) {
+      const int body = wcount & ~3;
+      if (lane == 0 && body) {
+        bulk_store(dst + g.out0 + w0, wout, (uint32_t)body * 4u);
+        bulk_commit();
+      }
+      if (lane < (wcount & 3)) dst[g.out0 + w0 + body + lane] = wout[body + lane];
+    }
+  }
+  if (lane == 0) bulk_wait_all();
+  if (tid == 0 && !ok) atomicExch(status, (int)NSORT_ETIMEOUT);
+}
+
 // ------------------------------------------------------------- host side
 
 namespace {
@@ -302,6 +480,10 @@ constexpr int MERGE_NT = 256;       // merge pass: 256 threads x 16 = 4096 outpu
 constexpr int MERGE_VT = 16;
 constexpr int PMERGE_NT = 256;
 constexpr int PMERGE_VT = 16;
+
+constexpr int TMA_MERGE_NT = 256;   // persistent merge pass: 256 threads x 15 = 3840 outputs
+constexpr int TMA_MERGE_VT = 15;
+constexpr int TMA_MERGE_TILE = TMA_MERGE_NT * TMA_MERGE_VT;
 
 constexpr int KEYS_SORT_TILE = KEYS_SORT_NT * 16;
 constexpr int PAIRS_SORT_TILE = PAIRS_SORT_NT * 16;
@@ -314,23 +496,42 @@ constexpr size_t PAIRS_SORT_SMEM =
 
 }  // namespace
 
+int64_t pair_tiles(int64_t n, int64_t run, int tile, int64_t *tpp_out) {
+  const int64_t tpp = (2 * run + tile - 1) / tile;
+  const int64_t full = n / (2 * run);
+  const int64_t rem = n - full * 2 * run;
+  if (tpp_out) *tpp_out = tpp;
+  return full * tpp + (rem + tile - 1) / tile;
+}
+
 Plan make_plan(int kind, uint64_t n) {
   Plan p;
   const bool pairs = kind == NSORT_KIND_PAIRS;
   p.n = (int64_t)n;
   p.sort_tile = pairs ? PAIRS_SORT_TILE : KEYS_SORT_TILE;
-  p.merge_tile = pairs ? PMERGE_TILE : MERGE_TILE;
+  // keys: the bulk-copy pass's tile; the staged-load fallback uses MERGE_TILE
+  p.merge_tile = pairs ? PMERGE_TILE : TMA_MERGE_TILE;
   const int64_t runs = (p.n + p.sort_tile - 1) / p.sort_tile;
   p.merge_passes = 0;
   while ((int64_t(1) << p.merge_passes) < runs) ++p.merge_passes;
-  p.num_merge_tiles = (p.n + p.merge_tile - 1) / p.merge_tile;
+  p.num_merge_tiles = (p.n + (pairs ? PMERGE_TILE : MERGE_TILE) - 1) / (pairs ? PMERGE_TILE : MERGE_TILE);
+  // splitters: enough for the power-of-two tiling and for the pair-aligned
+  // tiling of every pass
+  int64_t max_tiles = p.num_merge_tiles;
+  if (!pairs) {
+    for (int pass = 0; pass < p.merge_passes; ++pass) {
+      const int64_t t = pair_tiles(p.n, (int64_t)p.sort_tile << pass, TMA_MERGE_TILE, nullptr);
+      if (t > max_tiles) max_tiles = t;
+    }
+  }
   const size_t kb = align_up((size_t)n * 4, 256);
-  p.keys_off = 0;
-  p.vals_off = kb;
-  p.split_off = pairs ? 2 * kb : kb;
+  p.status_off = 0;
+  p.keys_off = 256;
+  p.vals_off = p.keys_off + kb;
+  p.split_off = pairs ? p.vals_off + kb : p.keys_off + kb;
   p.total = p.merge_passes == 0
                 ? 0
-                : p.split_off + align_up((size_t)(p.num_merge_tiles + 1) * sizeof(int64_t), 256);
+                : p.split_off + align_up((size_t)(max_tiles + 1) * sizeof(int64_t), 256);
   return p;
 }
 
@@ -410,9 +611,53 @@ static void launch_merge_pairs(const uint32_t *ks, const uint32_t *vs, uint32_t 
 }
 
 static void launch_partition(const uint32_t *src, int64_t n, int64_t run, const Plan &p,
-                             int64_t *split, cudaStream_t st) {
+                             int tile, int64_t *split, cudaStream_t st) {
   const unsigned blocks = (unsigned)((p.num_merge_tiles + 255) / 256);
-  partition_kernel<<<blocks, 256, 0, st>>>(src, n, run, p.merge_tile, p.num_merge_tiles, split);
+  partition_kernel<<<blocks, 256, 0, st>>>(src, n, run, tile, p.num_merge_tiles, split);
+}
+
+// Persistent merge pass: SMs x resident CTAs, found once per device.
+static int tma_merge_grid(int64_t tiles) {
+  static std::atomic<int> cached[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int g = dev < 64 ? cached[dev].load() : 0;
+  if (g == 0) {
+    int sms = 0, occ = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // prefer shared memory over L1: the pass keeps its data in shared memory
+    cudaFuncSetAttribute(merge_keys_tma_kernel<TMA_MERGE_NT, TMA_MERGE_VT, DT_U32>,
+                         cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(merge_keys_tma_kernel<TMA_MERGE_NT, TMA_MERGE_VT, DT_I32>,
+                         cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(merge_keys_tma_kernel<TMA_MERGE_NT, TMA_MERGE_VT, DT_F32>,
+                         cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &occ, merge_keys_tma_kernel<TMA_MERGE_NT, TMA_MERGE_VT, DT_U32>, TMA_MERGE_NT, 0);
+    g = (sms > 0 ? sms : 1) * (occ > 0 ? occ : 1);
+    if (dev < 64) cached[dev].store(g);
+  }
+  return (int)(tiles < g ? tiles : g);
+}
+
+static void launch_merge_keys_tma(const uint32_t *src, uint32_t *dst, int64_t n, int64_t run,
+                                  int64_t *split, int *status, int dt_out, cudaStream_t st) {
+  int64_t tpp = 0;
+  const int64_t tiles = pair_tiles(n, run, TMA_MERGE_TILE, &tpp);
+  {
+    TraceScope tr(TK_PARTITION, st);
+    partition_pairs_kernel<<<(unsigned)((tiles + 255) / 256), 256, 0, st>>>(
+        src, n, run, tpp, TMA_MERGE_TILE, tiles, split);
+  }
+  const unsigned grid = (unsigned)tma_merge_grid(tiles);
+  TraceScope tr(TK_MERGE_KEYS, st);
+#define NSORT_MKT(DT)                                                                   \
+  merge_keys_tma_kernel<TMA_MERGE_NT, TMA_MERGE_VT, DT><<<grid, TMA_MERGE_NT, 0, st>>>( \
+      src, dst, n, run, tpp, tiles, split, status)
+  if (dt_out == DT_U32) NSORT_MKT(DT_U32);
+  else if (dt_out == DT_I32) NSORT_MKT(DT_I32);
+  else NSORT_MKT(DT_F32);
+#undef NSORT_MKT
 }
 
 // ---- the sorts ------------------------------------------------------------
@@ -420,10 +665,15 @@ static void launch_partition(const uint32_t *src, int64_t n, int64_t run, const 
 int sort_keys_impl(const uint32_t *in, uint32_t *out, int64_t n, int dt, void *tmp,
                    cudaStream_t st) {
   const Plan p = make_plan(NSORT_KIND_KEYS, (uint64_t)n);
-  uint32_t *bufs[2] = {out, reinterpret_cast<uint32_t *>(static_cast<char *>(tmp) + p.keys_off)};
-  int64_t *split = p.merge_passes
-                       ? reinterpret_cast<int64_t *>(static_cast<char *>(tmp) + p.split_off)
-                       : nullptr;
+  char *t = static_cast<char *>(tmp);
+  uint32_t *bufs[2] = {out, p.merge_passes ? reinterpret_cast<uint32_t *>(t + p.keys_off) : nullptr};
+  int64_t *split = p.merge_passes ? reinterpret_cast<int64_t *>(t + p.split_off) : nullptr;
+  int *status = p.merge_passes ? reinterpret_cast<int *>(t + p.status_off) : nullptr;
+  if (status && cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess)
+    return launch_status("cudaMemsetAsync");
+  // the bulk-copy merge pass needs 16-byte aligned ping-pong buffers (the
+  // scratch always is); otherwise the staged-load pass is used
+  const bool tma = !(reinterpret_cast<uintptr_t>(out) & 15);
   int cur = p.merge_passes % 2;  // the last pass must land in bufs[0] == out
   const int64_t tiles = (n + p.sort_tile - 1) / p.sort_tile;
   {
@@ -433,14 +683,17 @@ int sort_keys_impl(const uint32_t *in, uint32_t *out, int64_t n, int dt, void *t
   int rc = launch_status("tile_sort_keys");
   for (int pass = 0; rc == NSORT_OK && pass < p.merge_passes; ++pass) {
     const int64_t run = (int64_t)p.sort_tile << pass;
-    {
-      TraceScope tr(TK_PARTITION, st);
-      launch_partition(bufs[cur], n, run, p, split, st);
-    }
-    {
+    const int dt_out = pass == p.merge_passes - 1 ? dt : DT_U32;
+    if (tma) {
+      launch_merge_keys_tma(bufs[cur], bufs[cur ^ 1], n, run, split, status, dt_out, st);
+    } else {
+      {
+        TraceScope tr(TK_PARTITION, st);
+        launch_partition(bufs[cur], n, run, p, MERGE_TILE, split, st);
+      }
       TraceScope tr(TK_MERGE_KEYS, st);
-      launch_merge_keys(bufs[cur], bufs[cur ^ 1], n, run, split,
-                        pass == p.merge_passes - 1 ? dt : DT_U32, (unsigned)p.num_merge_tiles, st);
+      launch_merge_keys(bufs[cur], bufs[cur ^ 1], n, run, split, dt_out,
+                        (unsigned)p.num_merge_tiles, st);
     }
     rc = launch_status("merge_keys");
     cur ^= 1;
@@ -457,6 +710,8 @@ int sort_pairs_impl(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, ui
   uint32_t *kb[2] = {kout, reinterpret_cast<uint32_t *>(t + p.keys_off)};
   uint32_t *vb[2] = {vout, reinterpret_cast<uint32_t *>(t + p.vals_off)};
   int64_t *split = p.merge_passes ? reinterpret_cast<int64_t *>(t + p.split_off) : nullptr;
+  if (p.merge_passes && cudaMemsetAsync(t + p.status_off, 0, sizeof(int), st) != cudaSuccess)
+    return launch_status("cudaMemsetAsync");
   int cur = p.merge_passes % 2;
   const int64_t tiles = (n + p.sort_tile - 1) / p.sort_tile;
   {
@@ -469,7 +724,7 @@ int sort_pairs_impl(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, ui
     const int64_t run = (int64_t)p.sort_tile << pass;
     {
       TraceScope tr(TK_PARTITION, st);
-      launch_partition(kb[cur], n, run, p, split, st);
+      launch_partition(kb[cur], n, run, p, PMERGE_TILE, split, st);
     }
     {
       TraceScope tr(TK_MERGE_PAIRS, st);

@@ -21,9 +21,10 @@ struct Plan {
   int merge_tile = 0;        // outputs per merge CTA
   int merge_passes = 0;      // ceil(log2(ceil(n / sort_tile)))
   int64_t num_merge_tiles = 0;
+  size_t status_off = 0;     // device status word (NSORT_OK / NSORT_ETIMEOUT)
   size_t keys_off = 0;       // ping-pong key buffer
   size_t vals_off = 0;       // ping-pong value buffer (pairs)
-  size_t split_off = 0;      // num_merge_tiles + 1 int64 splitters
+  size_t split_off = 0;      // int64 merge-path splitters, one per merge tile
   size_t total = 0;          // bytes of scratch (0 when one tile holds everything)
 };
 

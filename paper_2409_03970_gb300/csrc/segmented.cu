@@ -637,15 +637,3 @@ extern "C" int nsort_segmented(const void *d_keys_in, void *d_keys_out, const ui
   return NSORT_OK;
 }
 
-extern "C" int nsort_segmented_status(const void *d_tmp, void *stream) {
-  if (!d_tmp) return NSORT_EINVAL;
-  int status = 0;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (cudaMemcpyAsync(&status, d_tmp, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess) {
-    set_last_error(std::string("nsort_segmented_status: ") +
-                   cudaGetErrorString(cudaGetLastError()));
-    return NSORT_ECUDA;
-  }
-  return status;
-}

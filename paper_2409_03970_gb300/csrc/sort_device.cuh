@@ -240,6 +240,41 @@ __device__ __forceinline__ int64_t merge_path_global_warp(const uint32_t *A, int
   return lo;
 }
 
+// Merge path on unpadded shared memory: A and B are separate contiguous
+// runs (the merge pass stages them with bulk copies, which cannot pad).
+__device__ __forceinline__ int merge_path_plain(const uint32_t *s, int a0, int na, int b0, int nb,
+                                                int diag) {
+  int lo = diag - nb > 0 ? diag - nb : 0;
+  int hi = diag < na ? diag : na;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (s[a0 + mid] <= s[b0 + diag - 1 - mid]) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Serial merge on unpadded shared memory (indices into s): VT outputs of the
+// stable merge of s[a, a_end) and s[b, b_end).  Reads at most VT + 1
+// elements past the larger end.
+template <int VT>
+__device__ __forceinline__ void serial_merge_plain(const uint32_t *s, int a, int a_end, int b,
+                                                   int b_end, uint32_t (&out)[VT]) {
+  uint32_t ka = s[a];
+  uint32_t kb = s[b];
+#pragma unroll
+  for (int k = 0; k < VT; ++k) {
+    const bool take_a = (b >= b_end) || (a < a_end && ka <= kb);
+    out[k] = take_a ? ka : kb;
+    const int nx = (take_a ? a : b) + 1;
+    const uint32_t kn = s[nx];
+    a = take_a ? nx : a;
+    b = take_a ? b : nx;
+    ka = take_a ? kn : ka;
+    kb = take_a ? kb : kn;
+  }
+}
+
 // ---- serial merge (the serial half of the hybrid merger) ----------------
 // Produces VT outputs of the stable merge of s[a, a_end) and s[b, b_end)
 // (element indices, padded layout) into out[].  Branch-free: one compare,

@@ -66,8 +66,8 @@ def _load():
         lib.nsort_pairs.restype = i32
         lib.nsort_segmented.argtypes = [vp, vp, vp, vp, vp, u64, u64, i32, vp, sz, vp]
         lib.nsort_segmented.restype = i32
-        lib.nsort_segmented_status.argtypes = [vp, vp]
-        lib.nsort_segmented_status.restype = i32
+        lib.nsort_device_status.argtypes = [vp, vp]
+        lib.nsort_device_status.restype = i32
         lib.nsort_segmented_set_config.argtypes = [ctypes.POINTER(SegConfig)]
         lib.nsort_segmented_set_config.restype = i32
         lib.nsort_segmented_get_config.argtypes = [ctypes.POINTER(SegConfig)]
@@ -159,8 +159,9 @@ def nsort_segmented(keys_in, keys_out, vals_in, vals_out, offsets, nseg: int, n:
                                    _stream(stream))
 
 
-def nsort_segmented_status(tmp, stream=None) -> int:
-    return _load().nsort_segmented_status(_ptr(tmp), _stream(stream))
+def nsort_device_status(tmp, stream=None) -> int:
+    """Device status word of the last call that used scratch `tmp` (syncs)."""
+    return _load().nsort_device_status(_ptr(tmp), _stream(stream))
 
 
 def nsort_segmented_set_config(block_threads=512, tiny_width=16, small_ipt=16,
@@ -259,7 +260,7 @@ def sort_segmented(keys, offsets, vals=None, keys_out=None, vals_out=None, tmp=N
     if rc != OK:
         raise NsortError(rc, "nsort_segmented")
     if check:
-        st = nsort_segmented_status(tmp, stream)
+        st = nsort_device_status(tmp, stream)
         if st != OK:
             raise NsortError(st, "nsort_segmented (device status)")
     return keys_out if vals is None else (keys_out, vals_out)

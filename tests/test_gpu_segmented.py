@@ -61,7 +61,7 @@ def run_seg(ns, keys, off, dt, vals=None, inplace=False):
     tmp = ns.scratch(kind, n, nseg)
     rc = ns.nsort_segmented(kt, ko, vt, vo, ot, nseg, n, DT[dt], tmp, tmp.numel())
     assert rc == ns.OK, ns.lib().nsort_last_error()
-    assert ns.nsort_segmented_status(tmp) == ns.OK
+    assert ns.nsort_device_status(tmp) == ns.OK
     k = ko.cpu().numpy().view(np.uint32)
     return k if vals is None else (k, vo.cpu().numpy().view(np.uint32))
 
@@ -125,7 +125,7 @@ def test_malformed_offsets_reported(ns):
         tmp = ns.scratch(ns.KIND_SEGMENTED, 1000, len(bad) - 1)
         rc = ns.nsort_segmented(x, out, None, None, off, len(bad) - 1, 1000, 0, tmp, tmp.numel())
         assert rc == ns.OK
-        assert ns.nsort_segmented_status(tmp) == ns.EINVAL
+        assert ns.nsort_device_status(tmp) == ns.EINVAL
 
 
 def test_zero_one_principle_16_input_network_on_gpu(ns):
@@ -172,7 +172,7 @@ def test_cuda_graph_capture_and_replay(ns):
         g.replay()
         torch.cuda.synchronize()
         np.testing.assert_array_equal(ko.cpu().numpy().view(np.uint32), want)
-        assert ns.nsort_segmented_status(tmp) == ns.OK
+        assert ns.nsort_device_status(tmp) == ns.OK
 
 
 def test_batch_of_the_benchmark_shape(ns):
