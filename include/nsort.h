@@ -152,6 +152,57 @@ int nsort_segmented_get_config(nsort_seg_config *cfg);
 int nsort_keys_noalloc(const void *d_keys_in, void *d_keys_out, uint64_t n, int dtype,
                        void *stream);
 
+/* ---- serving: continuous batching of sort requests --------------------
+ * A context owns a scheduler thread, a pool of CUDA streams and a device
+ * memory budget.  Requests (device-resident inputs and outputs owned by the
+ * caller) are admitted as soon as a stream slot and budget for their scratch
+ * are free; small requests are co-batched into one segmented launch;
+ * admitted requests overlap on the device.  Each result is bit-identical to
+ * the plain call on the same input.  Paper: none — the serving layer is this
+ * library's extension around the Sec. 2.1 sort. */
+typedef struct nsort_ctx nsort_ctx;
+
+typedef struct {
+    int kind;                 /* NSORT_KIND_KEYS or NSORT_KIND_PAIRS */
+    int dtype;                /* nsort_dtype */
+    uint64_t n;
+    const void *d_keys_in;
+    void *d_keys_out;
+    const uint32_t *d_vals_in;  /* PAIRS only */
+    uint32_t *d_vals_out;       /* PAIRS only */
+} nsort_request;
+
+typedef struct {
+    double t_submit;   /* seconds on the host monotonic clock */
+    double t_admit;    /* scratch reserved, work enqueued */
+    double t_done;     /* completion observed by the scheduler */
+    int status;        /* nsort_status of the request */
+    int batched;       /* 1 when co-batched into a segmented launch */
+} nsort_timing;
+
+/* device: CUDA ordinal.  mem_budget_bytes: size of the scratch arena the
+ * context allocates once (cudaMalloc) and sub-allocates to admitted
+ * requests; a request whose scratch exceeds the whole arena is rejected
+ * with NSORT_ENOMEM at submit.  streams: concurrent stream slots (1..64).
+ * batch_max_keys: requests of at most this many keys are co-batched (0
+ * disables co-batching; streams = 1 and batch_max_keys = 0 is plain FIFO
+ * one-at-a-time sorting).  Returns NSORT_OK and *out, or an error. */
+int nsort_ctx_create(int device, size_t mem_budget_bytes, int streams,
+                     uint64_t batch_max_keys, nsort_ctx **out);
+/* Stops admitting, waits for every admitted request, stops the scheduler
+ * and frees the arena and the streams.  Requests still waiting for
+ * admission complete with status NSORT_EBUSY (cancelled). */
+void nsort_ctx_destroy(nsort_ctx *ctx);
+/* Enqueues a request (device buffers owned by the caller, which must not be
+ * touched until the request is done); never blocks on the device.  *ticket
+ * identifies it.  n = 0 completes at once. */
+int nsort_submit(nsort_ctx *ctx, const nsort_request *req, uint64_t *ticket);
+/* *done = 1 once the request completed (then *timing, if not NULL, is
+ * filled); NSORT_ENOTFOUND for an unknown ticket. */
+int nsort_poll(nsort_ctx *ctx, uint64_t ticket, int *done, nsort_timing *timing);
+/* Blocks until the request completed or timeout_ms passed (NSORT_ETIMEOUT). */
+int nsort_wait(nsort_ctx *ctx, uint64_t ticket, uint32_t timeout_ms);
+
 /* ---- tracing ------------------------------------------------------------
  * Per-kernel device time without a profiler.  While enabled, every kernel
  * launch of the library is bracketed by CUDA events recorded on the stream

@@ -1,0 +1,36 @@
+/*
+ * Test hooks of libnsort: the pure host-side policy of the sort server,
+ * exposed so that it can be checked on a machine without a GPU.  They make
+ * no CUDA call.  Paper: none (serving is this library's extension).
+ */
+#ifndef NSORT_TESTING_H
+#define NSORT_TESTING_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Runs the server's admission choice on a waiting queue of `count`
+ * requests (arrival order; kind, dtype and size each): which tickets the
+ * next free stream slot takes together.  Writes them to out (capacity
+ * `count`) and their number to *out_count. */
+int nsort_policy_pick_batch(const uint64_t *tickets, const int *kinds, const int *dtypes,
+                            const uint64_t *ns, int count, uint64_t batch_max_keys,
+                            int max_batch, uint64_t max_batch_keys, uint64_t *out,
+                            int *out_count);
+
+/* Replays allocations and releases on the server's scratch arena (first
+ * fit, 256-byte granules, coalescing).  ops[i] > 0 allocates ops[i] bytes
+ * and writes its offset (or -1 when nothing fits) to offsets[i];
+ * ops[i] < 0 releases the block of op number -ops[i]-1. */
+int nsort_policy_arena_replay(uint64_t capacity, const int64_t *ops, int nops,
+                              int64_t *offsets);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NSORT_TESTING_H */

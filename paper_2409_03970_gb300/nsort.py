@@ -26,6 +26,22 @@ _lock = threading.Lock()
 _lib = None
 
 
+class Request(ctypes.Structure):
+    """nsort_request."""
+    _fields_ = [("kind", ctypes.c_int), ("dtype", ctypes.c_int), ("n", ctypes.c_uint64),
+                ("d_keys_in", ctypes.c_void_p), ("d_keys_out", ctypes.c_void_p),
+                ("d_vals_in", ctypes.c_void_p), ("d_vals_out", ctypes.c_void_p)]
+
+
+class Timing(ctypes.Structure):
+    """nsort_timing: host monotonic-clock seconds."""
+    _fields_ = [("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("status", ctypes.c_int), ("batched", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class SegConfig(ctypes.Structure):
     """nsort_seg_config: tunables of the segmented sort."""
     _fields_ = [("block_threads", ctypes.c_int), ("tiny_width", ctypes.c_int),
@@ -72,6 +88,22 @@ def _load():
         lib.nsort_segmented_set_config.restype = i32
         lib.nsort_segmented_get_config.argtypes = [ctypes.POINTER(SegConfig)]
         lib.nsort_segmented_get_config.restype = i32
+        lib.nsort_ctx_create.argtypes = [i32, sz, i32, u64, ctypes.POINTER(vp)]
+        lib.nsort_ctx_create.restype = i32
+        lib.nsort_ctx_destroy.argtypes = [vp]
+        lib.nsort_ctx_destroy.restype = None
+        lib.nsort_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(u64)]
+        lib.nsort_submit.restype = i32
+        lib.nsort_poll.argtypes = [vp, u64, ip, ctypes.POINTER(Timing)]
+        lib.nsort_poll.restype = i32
+        lib.nsort_wait.argtypes = [vp, u64, ctypes.c_uint32]
+        lib.nsort_wait.restype = i32
+        u64p = ctypes.POINTER(u64)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        lib.nsort_policy_pick_batch.argtypes = [u64p, ip, ip, u64p, i32, u64, i32, u64, u64p, ip]
+        lib.nsort_policy_pick_batch.restype = i32
+        lib.nsort_policy_arena_replay.argtypes = [u64, i64p, i32, i64p]
+        lib.nsort_policy_arena_replay.restype = i32
         lib.nsort_keys_noalloc.argtypes = [vp, vp, u64, i32, vp]
         lib.nsort_keys_noalloc.restype = i32
         lib.nsort_trace_enable.argtypes = [i32]
@@ -176,6 +208,105 @@ def nsort_segmented_get_config() -> dict:
     if rc != OK:
         raise NsortError(rc, "nsort_segmented_get_config")
     return cfg.as_dict()
+
+
+# ---- serving ---------------------------------------------------------------
+
+def nsort_ctx_create(device: int = 0, mem_budget_bytes: int = 1 << 30, streams: int = 4,
+                     batch_max_keys: int = 1 << 16) -> int:
+    """A sort-serving context (opaque handle)."""
+    h = ctypes.c_void_p()
+    rc = _load().nsort_ctx_create(device, mem_budget_bytes, streams, batch_max_keys,
+                                  ctypes.byref(h))
+    if rc != OK:
+        raise NsortError(rc, "nsort_ctx_create")
+    return h.value
+
+
+def nsort_ctx_destroy(ctx: int) -> None:
+    _load().nsort_ctx_destroy(ctx)
+
+
+def nsort_submit(ctx: int, kind: int, dtype: int, n: int, keys_in, keys_out, vals_in=None,
+                 vals_out=None) -> int:
+    """Submits a request; returns its ticket."""
+    req = Request(kind, dtype, n, _ptr(keys_in), _ptr(keys_out), _ptr(vals_in), _ptr(vals_out))
+    t = ctypes.c_uint64()
+    rc = _load().nsort_submit(ctx, ctypes.byref(req), ctypes.byref(t))
+    if rc != OK:
+        raise NsortError(rc, "nsort_submit")
+    return t.value
+
+
+def nsort_poll(ctx: int, ticket: int):
+    """(done, timing dict or None)."""
+    done = ctypes.c_int()
+    tm = Timing()
+    rc = _load().nsort_poll(ctx, ticket, ctypes.byref(done), ctypes.byref(tm))
+    if rc != OK:
+        raise NsortError(rc, "nsort_poll")
+    return bool(done.value), (tm.as_dict() if done.value else None)
+
+
+def nsort_wait(ctx: int, ticket: int, timeout_ms: int = 60000) -> int:
+    return _load().nsort_wait(ctx, ticket, timeout_ms)
+
+
+class SortServer:
+    """Context manager around an nsort serving context."""
+
+    def __init__(self, device=0, mem_budget_bytes=1 << 30, streams=4, batch_max_keys=1 << 16):
+        self.ctx = nsort_ctx_create(device, mem_budget_bytes, streams, batch_max_keys)
+
+    def submit(self, keys_in, keys_out, vals_in=None, vals_out=None, n=None, dtype=None):
+        kind = KIND_KEYS if vals_in is None else KIND_PAIRS
+        n = keys_in.numel() if n is None else n
+        dtype = dtype_code(keys_in) if dtype is None else dtype
+        return nsort_submit(self.ctx, kind, dtype, n, keys_in, keys_out, vals_in, vals_out)
+
+    def poll(self, ticket):
+        return nsort_poll(self.ctx, ticket)
+
+    def wait(self, ticket, timeout_ms=60000):
+        return nsort_wait(self.ctx, ticket, timeout_ms)
+
+    def close(self):
+        if self.ctx:
+            nsort_ctx_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def policy_pick_batch(queue, batch_max_keys, max_batch=4096, max_batch_keys=1 << 24):
+    """The server's admission choice for a queue of (ticket, kind, dtype, n)."""
+    m = len(queue)
+    T = (ctypes.c_uint64 * max(m, 1))(*[q[0] for q in queue])
+    K = (ctypes.c_int * max(m, 1))(*[q[1] for q in queue])
+    D = (ctypes.c_int * max(m, 1))(*[q[2] for q in queue])
+    N = (ctypes.c_uint64 * max(m, 1))(*[q[3] for q in queue])
+    out = (ctypes.c_uint64 * max(m, 1))()
+    cnt = ctypes.c_int()
+    rc = _load().nsort_policy_pick_batch(T, K, D, N, m, batch_max_keys, max_batch, max_batch_keys,
+                                         out, ctypes.byref(cnt))
+    if rc != OK:
+        raise NsortError(rc, "nsort_policy_pick_batch")
+    return [out[i] for i in range(cnt.value)]
+
+
+def policy_arena_replay(capacity, ops):
+    """Offsets the server's arena gives for a list of alloc (>0) / release (<0) ops."""
+    m = len(ops)
+    O = (ctypes.c_int64 * max(m, 1))(*ops)
+    R = (ctypes.c_int64 * max(m, 1))()
+    rc = _load().nsort_policy_arena_replay(capacity, O, m, R)
+    if rc != OK:
+        raise NsortError(rc, "nsort_policy_arena_replay")
+    return [R[i] for i in range(m)]
 
 
 NOALLOC_MAX_KEYS = 1 << 20
