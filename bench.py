@@ -49,6 +49,14 @@ def parse():
     ap.add_argument("--dtype", choices=["u32", "i32", "f32"], default="u32")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched (segmented) and served measurements")
+    ap.add_argument("--workload", choices=["plain", "segmented", "served"], default="plain",
+                    help="plain: the headline line (with batched/served extras); segmented / "
+                         "served: that measurement alone, as its own line")
+    ap.add_argument("--served-duration", type=float, default=10.0,
+                    help="seconds of Poisson arrivals in the served measurement (60 = full)")
+    ap.add_argument("--segments", type=int, default=100_000)
     return ap.parse_args()
 
 
@@ -233,6 +241,178 @@ def run_reference(args, rank, world):
     }), flush=True)
 
 
+# ---- batched (segmented) and served measurements -----------------------------
+
+def bench_batched(nsort, torch, nseg: int, reps: int = 5):
+    """100,000 uint32 arrays (lengths log-uniform in [1, 65536], uniform keys)
+    sorted by one graph-captured nsort_segmented launch with the autotuned
+    configuration, against one plain nsort_keys call per array."""
+    from paper_2409_03970_gb300 import autotune, inputs
+    off = inputs.segment_offsets(nseg, seed=0)
+    total = int(off[-1])
+    keys = inputs.keys(total, "u32", "uniform", seed=0)
+    kt = torch.from_numpy(keys.view(np.int32)).cuda()
+    del keys
+    ot = torch.from_numpy(off).cuda()
+    ko = torch.empty_like(kt)
+    t0 = time.perf_counter()
+    tune = autotune.tune_segmented(kt, ot, reps=2)
+    tune_s = time.perf_counter() - t0
+    tmp = nsort.scratch(nsort.KIND_SEGMENTED, total, nseg)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for _ in range(2):
+            assert nsort.nsort_segmented(kt, ko, None, None, ot, nseg, total, nsort.U32, tmp,
+                                         tmp.numel(), s) == nsort.OK
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        nsort.nsort_segmented(kt, ko, None, None, ot, nseg, total, nsort.U32, tmp, tmp.numel(), s)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g.replay()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    ms_b = e0.elapsed_time(e1) / reps
+    assert nsort.nsort_device_status(tmp) == nsort.OK
+    batched_out = ko.clone()
+    # one plain launch (nsort_keys) per array, on one stream
+    lens = np.diff(off)
+    ptmp = nsort.scratch(nsort.KIND_KEYS, int(lens.max()))
+    pb = ptmp.numel()
+    st = torch.cuda.current_stream()
+    sh = st.cuda_stream
+    kin, kout = kt.data_ptr(), ko.data_ptr()
+    lib = nsort.lib()
+    offs = off.tolist()
+    ms_p = []
+    for _ in range(2):
+        torch.cuda.synchronize()
+        e0.record(st)
+        for i in range(nseg):
+            o, L = offs[i], offs[i + 1] - offs[i]
+            lib.nsort_keys(kin + 4 * o, kout + 4 * o, L, 0, ptmp.data_ptr(), pb, sh)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms_p.append(e0.elapsed_time(e1))
+    same = bool(torch.equal(batched_out, ko))
+    return {"metric": "GKeys/s", "workload": f"{nseg} uint32 arrays, lengths log-uniform in "
+            f"[1, 65536], {total} keys, uniform, seed 0",
+            "batched_gkeys_s": total / ms_b / 1e6, "batched_ms": ms_b,
+            "plain_per_array_gkeys_s": total / min(ms_p) / 1e6, "plain_per_array_ms": min(ms_p),
+            "speedup": min(ms_p) / ms_b, "identical_results": same,
+            "launch": "one graph-captured nsort_segmented (3 set-up kernels + 1 persistent)",
+            "autotuned_config": tune["config"], "autotune_seconds": tune_s,
+            "candidates": len(tune["table"])}
+
+
+def bench_served(nsort, torch, duration: float, rate: float = 2000.0, budget: int = 64 << 30,
+                 streams: int = 8, batch_max_keys: int = 1 << 16, seed: int = 0):
+    """Open-loop Poisson arrivals (rate/s for `duration` s), sizes log-uniform
+    in [2^10, 2^26], dtype uniform over {u32, i32, f32, f32 key + u32 value},
+    against a 64 GB scratch budget.  Latency = completion - scheduled arrival.
+    The same schedule runs through the continuous-batching server and through
+    plain FIFO sorting (one request at a time, no batching)."""
+    from paper_2409_03970_gb300 import inputs
+    count = int(rate * duration)
+    u = inputs.unit_double(inputs.counter_u64(seed, inputs.S_SERVE, 0, count))
+    gaps = -np.log1p(-u) / rate
+    arrival = np.cumsum(gaps)
+    us = inputs.unit_double(inputs.counter_u64(seed, inputs.S_SERVE + 1, 0, count))
+    sizes = np.floor(np.exp2(10 + 16 * us)).astype(np.int64)
+    modes = (inputs.counter_u32(seed, inputs.S_SERVE + 2, 0, count) % 4).astype(np.int64)
+    starts = (inputs.counter_u64(seed, inputs.S_SERVE + 3, 0, count) %
+              np.uint64((1 << 28) - (1 << 26))).astype(np.int64) & ~3
+    pool_k = torch.from_numpy(inputs.keys(1 << 28, "u32", "uniform", seed=seed).view(np.int32)).cuda()
+    pool_v = torch.arange(1 << 28, dtype=torch.int32, device="cuda")
+    ring = 1 << 30
+    out_k = torch.empty(ring, dtype=torch.int32, device="cuda")
+    out_v = torch.empty(ring, dtype=torch.int32, device="cuda")
+    total_keys = int(sizes.sum())
+    state = {"count": count, "total_keys": total_keys}
+
+    def run(streams_, batch_):
+        count = state["count"]
+        total_keys = state["total_keys"]
+        srv = nsort.SortServer(0, budget, streams_, batch_)
+        # warm-up: one request of each mode and a small batch
+        for m in range(4):
+            for n in (1 << 12, 1 << 20):
+                kind = nsort.KIND_PAIRS if m == 3 else nsort.KIND_KEYS
+                dt = [nsort.U32, nsort.I32, nsort.F32, nsort.F32][m]
+                t = nsort.nsort_submit(srv.ctx, kind, dt, n, pool_k, out_k,
+                                       pool_v if m == 3 else None, out_v if m == 3 else None)
+                srv.wait(t)
+        kb, vb = pool_k.data_ptr(), pool_v.data_ptr()
+        ob, ovb = out_k.data_ptr(), out_v.data_ptr()
+        tickets = []
+        rpos = 0
+        t0 = time.monotonic()
+        for i in range(count):
+            n = int(sizes[i])
+            if rpos + n > ring:
+                rpos = 0
+            m = int(modes[i])
+            kind = nsort.KIND_PAIRS if m == 3 else nsort.KIND_KEYS
+            dt = [nsort.U32, nsort.I32, nsort.F32, nsort.F32][m]
+            st = int(starts[i])
+            due = t0 + arrival[i]
+            while True:
+                d = due - time.monotonic()
+                if d <= 0:
+                    break
+                if d > 0.002:
+                    time.sleep(d - 0.001)
+            tickets.append(nsort.nsort_submit(srv.ctx, kind, dt, n, kb + 4 * st, ob + 4 * rpos,
+                                              vb + 4 * st if m == 3 else None,
+                                              ovb + 4 * rpos if m == 3 else None))
+            rpos = (rpos + n + 3) & ~3
+        done_t = np.empty(count)
+        batched = 0
+        for i, t in enumerate(tickets):
+            rc = srv.wait(t, 600000)
+            if rc != nsort.OK:
+                raise nsort.NsortError(rc, "served request")
+            _, tm = srv.poll(t)
+            done_t[i] = tm["t_done"]
+            batched += tm["batched"]
+        srv.close()
+        lat = (done_t - (t0 + arrival)) * 1e3
+        span = done_t.max() - t0
+        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_ms": float(lat.mean()), "gkeys_s": total_keys / span / 1e9,
+                "makespan_s": float(span), "batched_requests": int(batched),
+                "streams": streams_, "batch_max_keys": batch_}
+
+    served = run(streams, batch_max_keys)
+    fifo = run(1, 0)
+    # saturation: the first 2,000 requests all due at once (closed loop), so
+    # keys/s measures capacity rather than the offered load
+    arrival_open = arrival.copy()
+    sat_n = min(count, 2000)
+    arrival[:] = 0.0
+    state.update(count=sat_n, total_keys=int(sizes[:sat_n].sum()))
+    sat_served = run(streams, batch_max_keys)
+    sat_fifo = run(1, 0)
+    arrival[:] = arrival_open
+    state.update(count=count, total_keys=total_keys)
+    return {"workload": f"Poisson arrivals at {rate:g}/s for {duration:g} s ({count} requests, "
+                        f"{total_keys} keys), sizes log-uniform in [2^10, 2^26], dtype uniform over "
+                        f"u32/i32/f32/f32+u32 pairs, {budget >> 30} GB scratch budget",
+            "served": served, "plain_fifo": fifo,
+            "p99_speedup": fifo["p99_ms"] / served["p99_ms"],
+            "throughput_speedup": served["gkeys_s"] / fifo["gkeys_s"],
+            "saturated": {"requests": sat_n, "served_gkeys_s": sat_served["gkeys_s"],
+                          "plain_fifo_gkeys_s": sat_fifo["gkeys_s"],
+                          "served_p99_ms": sat_served["p99_ms"],
+                          "plain_fifo_p99_ms": sat_fifo["p99_ms"],
+                          "throughput_speedup": sat_served["gkeys_s"] / sat_fifo["gkeys_s"]},
+            "latency": "completion minus scheduled arrival (open loop)"}
+
+
 # ---- the GPU benchmark -----------------------------------------------------------
 
 def main():
@@ -252,6 +432,23 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     nbuild.build()
     nsort.lib()
+
+    if args.workload != "plain":
+        if rank == 0:
+            if args.workload == "segmented":
+                r = bench_batched(nsort, torch, args.segments)
+                line = {"metric": "GKeys/s, batched segmented sort vs one plain launch per array",
+                        "value": r["batched_gkeys_s"], "unit": "GKeys/s", "n_gpus": 1,
+                        "higher_is_better": True, "data": "synthetic", "dtype": "u32",
+                        "config": r, "vs_baseline": None}
+            else:
+                r = bench_served(nsort, torch, args.served_duration)
+                line = {"metric": "served sort stream: keys/s and p50/p99 latency vs plain FIFO",
+                        "value": r["served"]["gkeys_s"], "unit": "GKeys/s", "n_gpus": 1,
+                        "higher_is_better": True, "data": "synthetic", "dtype": "mixed",
+                        "config": r, "vs_baseline": None}
+            print(json.dumps(line), flush=True)
+        return
 
     n = 1 << args.log2n
     code = {"u32": nsort.U32, "i32": nsort.I32, "f32": nsort.F32}[args.dtype]
@@ -342,6 +539,15 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.dtype)
 
+    batched = served = None
+    if rank == 0 and world == 1 and not args.no_extras:
+        del x, out, tmp, host_in
+        torch.cuda.empty_cache()
+        batched = bench_batched(nsort, torch, args.segments)
+        torch.cuda.empty_cache()
+        served = bench_served(nsort, torch, args.served_duration)
+        torch.cuda.empty_cache()
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -362,6 +568,8 @@ def main():
             "kernels": {k: {"launches": v["launches"], "ms_per_launch": v["total_ms"] / v["launches"]}
                         for k, v in trace.items()},
             "clocks": clk,
+            "batched": batched,
+            "served": served,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
