@@ -452,9 +452,14 @@ __global__ void __launch_bounds__(NT, 4) merge_keys_tma_kernel(
     const int wcount = g.count - w0 < WOUT ? g.count - w0 : WOUT;
     if (lane == 0) bulk_wait_read_all();   // the warp's previous store has left wout
     __syncwarp();
+    if (g.count == TILE) {
 #pragma unroll
-    for (int k = 0; k < VT; ++k)
-      if (tid * VT + k < g.count) wout[lane * VT + k] = from_key(o[k], DT_OUT);
+      for (int k = 0; k < VT; ++k) wout[lane * VT + k] = from_key(o[k], DT_OUT);
+    } else {
+#pragma unroll
+      for (int k = 0; k < VT; ++k)
+        if (tid * VT + k < g.count) wout[lane * VT + k] = from_key(o[k], DT_OUT);
+    }
     fence_proxy_async_smem();
     __syncwarp();
     if (wcount > 0) {
@@ -481,8 +486,8 @@ constexpr int MERGE_VT = 16;
 constexpr int PMERGE_NT = 256;
 constexpr int PMERGE_VT = 16;
 
-constexpr int TMA_MERGE_NT = 256;   // persistent merge pass: 256 threads x 15 = 3840 outputs
-constexpr int TMA_MERGE_VT = 15;
+constexpr int TMA_MERGE_NT = 128;   // persistent merge pass: 128 threads x 31 = 3968 outputs
+constexpr int TMA_MERGE_VT = 31;
 constexpr int TMA_MERGE_TILE = TMA_MERGE_NT * TMA_MERGE_VT;
 
 constexpr int KEYS_SORT_TILE = KEYS_SORT_NT * 16;
