@@ -135,7 +135,7 @@ int nsort_segmented_get_config(nsort_seg_config *cfg);
  * pool, a fixed arena sized at start-up) or they run where a cudaMalloc is
  * not allowed because it may block or synchronise the device.  Same result
  * as nsort_keys, but no scratch argument: the scratch is one fixed array in
- * the library's device global memory (about 4.03 MiB), present on every GPU
+ * the library's device global memory (about 4.1 MiB), present on every GPU
  * that loads the library until the process exits.  The paper has no
  * counterpart; this is an interface for such callers.
  *  - n up to NSORT_NOALLOC_MAX_KEYS; larger n returns NSORT_ENOMEM with an

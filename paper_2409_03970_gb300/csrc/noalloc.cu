@@ -25,13 +25,16 @@ namespace nsort {
 
 namespace {
 
-// Scratch of a plain key sort of NSORT_NOALLOC_MAX_KEYS keys: one ping-pong
-// copy of the keys plus one int64 merge-path splitter per merge tile, sized
-// for merge tiles of 256 keys or more, each part rounded up to 256 bytes
-// (about 4.03 MiB in all).
+// Scratch of a plain key sort of NSORT_NOALLOC_MAX_KEYS keys, laid out as
+// nsort_keys lays out its scratch: the device status word, one ping-pong
+// copy of the keys, one int64 merge-path splitter per merge tile (sized for
+// merge tiles of 256 keys or more) and every 64th key of a pass's output;
+// each part rounded up to 256 bytes (about 4.1 MiB in all).
+constexpr size_t kStatusBytes = 256;
 constexpr size_t kKeysBytes = size_t(NSORT_NOALLOC_MAX_KEYS) * 4;
 constexpr size_t kSplitBytes = ((NSORT_NOALLOC_MAX_KEYS / 256 + 2) * 8 + 255) / 256 * 256;
-constexpr size_t kScratchBytes = kKeysBytes + kSplitBytes;
+constexpr size_t kSampleBytes = ((NSORT_NOALLOC_MAX_KEYS / 64 + 2) * 4 + 255) / 256 * 256;
+constexpr size_t kScratchBytes = kStatusBytes + kKeysBytes + kSplitBytes + kSampleBytes;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 

@@ -95,9 +95,14 @@ __device__ __forceinline__ bool aligned16(const void *p) {
 // applied on load); FINAL maps the keys back on store (the tile sort is the
 // whole sort when n fits one tile).  in may equal out: each CTA reads its
 // whole tile before its first barrier and writes it after its last.
+// Every SAMPLE-th output key of a sort stage (tile sort or merge pass) is
+// also written to a sample array; the next pass's partition searches the
+// samples first (section "sampled partition" below).
+constexpr int SAMPLE = 64;
+
 template <int NT, int DT, bool FINAL>
 __global__ void __launch_bounds__(NT) tile_sort_keys_kernel(const uint32_t *in, uint32_t *out,
-                                                            int64_t n) {
+                                                            int64_t n, uint32_t *samp) {
   constexpr int TILE = NT * 16;
   __shared__ uint32_t s[merge_smem_len<uint32_t>(TILE, 16)];
   const int tid = threadIdx.x;
@@ -127,6 +132,9 @@ __global__ void __launch_bounds__(NT) tile_sort_keys_kernel(const uint32_t *in, 
   }
   sort_tile_in_block<NT>(r, s);
   store_run<16, FINAL ? DT : DT_U32>(r, out + base, count, full);
+  static_assert(SAMPLE % 16 == 0, "a sample starts a thread's run of 16");
+  if (!FINAL && samp && !(tid & (SAMPLE / 16 - 1)) && tid * 16 < count)
+    store_keep_in_l2(samp + (base + tid * 16) / SAMPLE, r[0]);
 }
 
 // Tile sort, key/value pairs.  The networks sort 64-bit composites
@@ -346,68 +354,139 @@ __global__ void partition_pairs_kernel(const uint32_t *__restrict__ src, int64_t
   split[t] = merge_path_global(src + pair0, la, src + pair0 + la, lb, j * tile);
 }
 
+// Sampled partition for the pair-aligned tiling.  SA / SB are the samples
+// A[64q] / B[64r] written by the previous stage.  A merge-path search on the
+// samples at diagonal floor(d/64) gives qs; the true co-rank i* then lies in
+// [64(qs-1)+1, 64(qs+2)]: A[64(qs-1)] has at most 64(qs-1) + 64(floor(d/64)
+// - qs) < d elements before it in the merge, and A[64(qs+2)] at least
+// 64(qs+2) + 64(floor(d/64) - qs - 1) + 1 > d.  The full arrays are then
+// searched in that window only, the merge-path conditions are checked at
+// the result, and a full search is done if they fail, so the splitter is
+// exact whatever the samples say.
+__global__ void partition_sampled_kernel(const uint32_t *__restrict__ src,
+                                         const uint32_t *__restrict__ samp, int64_t n,
+                                         int64_t run, int64_t tpp, int tile, int64_t num_tiles,
+                                         int64_t *__restrict__ split) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= num_tiles) return;
+  const int64_t pair = t / tpp;
+  const int64_t j = t - pair * tpp;
+  const int64_t pair0 = pair * 2 * run;
+  const int64_t la = n - pair0 < run ? n - pair0 : run;
+  const int64_t rest = n - pair0 - run;
+  const int64_t lb = rest <= 0 ? 0 : (rest < run ? rest : run);
+  const int64_t d = j * tile;
+  const uint32_t *A = src + pair0;
+  const uint32_t *B = A + la;
+  const int64_t lo = d - lb > 0 ? d - lb : 0;
+  const int64_t hi = d < la ? d : la;
+  const int64_t qs = merge_path_global(samp + pair0 / SAMPLE, (la + SAMPLE - 1) / SAMPLE,
+                                       samp + (pair0 + la) / SAMPLE, (lb + SAMPLE - 1) / SAMPLE,
+                                       d / SAMPLE);
+  int64_t w0 = SAMPLE * (qs - 1) + 1, w1 = SAMPLE * (qs + 2);
+  w0 = w0 > lo ? w0 : lo;
+  w1 = w1 < hi ? w1 : hi;
+  int64_t i = w0 <= w1 ? w0 : lo, e = w0 <= w1 ? w1 : hi;
+  while (i < e) {
+    const int64_t mid = (i + e) >> 1;
+    if (__ldg(A + mid) <= __ldg(B + (d - 1 - mid))) i = mid + 1;
+    else e = mid;
+  }
+  const bool ok = i >= lo && i <= hi &&
+                  (i == 0 || d - i >= lb || __ldg(A + i - 1) <= __ldg(B + (d - i))) &&
+                  (i >= la || d - i == 0 || __ldg(B + (d - i - 1)) < __ldg(A + i));
+  split[t] = ok ? i : merge_path_global(A, la, B, lb, d);
+}
+
 // Where a tile's slices sit in its shared-memory buffer.  The A window
 // starts at the 16-byte boundary below a_off, so A[i] is at sh_a + i; the B
-// window starts at the next 16-byte boundary after A.
+// window starts at the first 16-byte boundary at least SENT elements after
+// A's end, leaving room for the largest-key sentinels of the unchecked
+// serial merge.
+constexpr int SENT = 32;
 struct SmemSlices {
   int sh_a, base_b, sh_b;
 };
 __device__ __forceinline__ SmemSlices smem_slices(const PairTile &g) {
   SmemSlices l;
   l.sh_a = (int)(g.a_off & 3);
-  l.base_b = (l.sh_a + g.na + 3) & ~3;
+  l.base_b = (l.sh_a + g.na + SENT + 3) & ~3;
   l.sh_b = (int)(g.b_off & 3);
   return l;
 }
 
-// Issues the bulk copies of tile g's slices into buf (thread 0 only).  The
-// windows are rounded to 16 bytes and clipped at n_al = n & ~3; elements
-// beyond n_al (at most 3 per slice, only at the very end of the array) are
-// loaded separately with ordinary loads.
-__device__ __forceinline__ void issue_tile_loads(const uint32_t *src, int64_t n_al,
-                                                 const PairTile &g, uint32_t *buf, uint64_t *bar) {
+// Prepares tile g in buffer buf (run by the 32 lanes of warp 0, into a
+// buffer no other thread is using): bulk copies of the 16-byte-aligned
+// bodies of both slices (rounded down at the end, so the copies never write
+// past a slice), ordinary loads of the ragged ends (at most 3 elements per
+// slice), and SENT largest-key sentinels after each slice.  The plain writes
+// and the bulk copies touch disjoint shared memory; the plain writes are
+// ordered before the bulk copies that later reuse this buffer by the proxy
+// fence, and before the merge by the CTA barrier that follows the wait.
+__device__ __forceinline__ void prepare_tile(const uint32_t *__restrict__ src, const PairTile &g,
+                                             uint32_t *buf, uint64_t *bar, int lane) {
   const SmemSlices l = smem_slices(g);
-  int64_t a0 = g.a_off & ~int64_t(3), a1 = (g.a_off + g.na + 3) & ~int64_t(3);
-  int64_t b0 = g.b_off & ~int64_t(3), b1 = (g.b_off + g.nb + 3) & ~int64_t(3);
-  if (a1 > n_al) a1 = n_al;
-  if (b1 > n_al) b1 = n_al;
-  const uint32_t bytes_a = (g.na > 0 && a1 > a0) ? (uint32_t)((a1 - a0) * 4) : 0u;
-  const uint32_t bytes_b = (g.nb > 0 && b1 > b0) ? (uint32_t)((b1 - b0) * 4) : 0u;
-  mbar_arrive_expect_tx(bar, bytes_a + bytes_b);
-  if (bytes_a) bulk_load(buf, src + a0, bytes_a, bar);
-  if (bytes_b) bulk_load(buf + l.base_b, src + b0, bytes_b, bar);
+  const int a0 = l.sh_a, b0 = l.base_b + l.sh_b;
+  const int64_t aw0 = g.a_off & ~int64_t(3), aw1 = (g.a_off + g.na) & ~int64_t(3);
+  const int64_t bw0 = g.b_off & ~int64_t(3), bw1 = (g.b_off + g.nb) & ~int64_t(3);
+  if (lane < 3) {
+    const int64_t i = aw1 + lane;
+    if (i >= g.a_off && i < g.a_off + g.na) buf[a0 + (int)(i - g.a_off)] = __ldg(src + i);
+  } else if (lane < 6) {
+    const int64_t i = bw1 + (lane - 3);
+    if (i >= g.b_off && i < g.b_off + g.nb) buf[b0 + (int)(i - g.b_off)] = __ldg(src + i);
+  }
+  static_assert(SENT == 32, "one sentinel per lane and slice");
+  buf[a0 + g.na + lane] = 0xFFFFFFFFu;
+  buf[b0 + g.nb + lane] = 0xFFFFFFFFu;
+  fence_proxy_async_smem();
+  __syncwarp();
+  if (lane == 0) {
+    const uint32_t bytes_a = aw1 > aw0 ? (uint32_t)((aw1 - aw0) * 4) : 0u;
+    const uint32_t bytes_b = bw1 > bw0 ? (uint32_t)((bw1 - bw0) * 4) : 0u;
+    mbar_arrive_expect_tx(bar, bytes_a + bytes_b);
+    if (bytes_a) bulk_load(buf, src + aw0, bytes_a, bar);
+    if (bytes_b) bulk_load(buf + l.base_b, src + bw0, bytes_b, bar);
+  }
 }
 
 // Per tile, one CTA-wide barrier: after it, every thread is done with the
-// previous tile, so thread 0 can reuse that buffer for the next tile's
-// copies while the CTA merges this one.  Each warp's outputs are contiguous
-// (32 * VT keys), so each warp stages and bulk-stores its own part with
-// warp-level synchronisation only.
+// previous tile, so warp 0 can prepare the next tile in that buffer while
+// the CTA merges this one.  Each warp's outputs are contiguous (32 * VT
+// keys), so each warp stages and bulk-stores its own part with warp-level
+// synchronisation only.
 template <int NT, int VT, int DT_OUT>
 __global__ void __launch_bounds__(NT, 4) merge_keys_tma_kernel(
     const uint32_t *__restrict__ src, uint32_t *__restrict__ dst, int64_t n, int64_t run,
-    int64_t tpp, int64_t num_tiles, const int64_t *__restrict__ split, int *status) {
+    int64_t tpp, int64_t num_tiles, const int64_t *__restrict__ split, int *status,
+    uint32_t *samp) {
   constexpr int TILE = NT * VT;
   constexpr int WOUT = 32 * VT;                       // outputs per warp
-  constexpr int IN_LEN = (TILE + 12 + VT + 2 + 3) & ~3;
+  // A window + sentinels, B window + sentinels, rounding slack
+  constexpr int IN_LEN = (TILE + 2 * SENT + 16) & ~3;
+  static_assert(SENT >= VT + 1, "each run needs VT sentinels past its end");
   static_assert(WOUT % 4 == 0, "warp output slices must be 16-byte multiples");
-  __shared__ __align__(128) uint32_t in_buf[2][IN_LEN];
-  __shared__ __align__(128) uint32_t out_buf[TILE];
+  static_assert(WOUT <= 32 * SAMPLE, "one sample per lane and warp slice");
+  // dynamic shared memory: [in_buf 0][in_buf 1][out_buf] (tma_merge_smem_bytes)
+  extern __shared__ __align__(128) unsigned char tma_smem[];
+  uint32_t(*in_buf)[IN_LEN] = reinterpret_cast<uint32_t(*)[IN_LEN]>(tma_smem);
+  uint32_t *out_buf = reinterpret_cast<uint32_t *>(tma_smem) + 2 * IN_LEN;
   __shared__ __align__(8) uint64_t bar[2];
-  __shared__ PairTile desc[2];   // geometry of the tile in each buffer, written by thread 0
+  __shared__ PairTile desc[2];   // geometry of the tile in each buffer, written by warp 0
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int warp = tid >> 5;
-  const int64_t n_al = n & ~int64_t(3);
   int64_t t = blockIdx.x;
   if (tid == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     fence_mbar_init();
-    if (t < num_tiles) {
-      desc[0] = pair_tile(t, n, run, tpp, TILE, split);
-      issue_tile_loads(src, n_al, desc[0], in_buf[0], &bar[0]);
-    }
+  }
+  __syncthreads();
+  if (warp == 0 && t < num_tiles) {
+    if (lane == 0) desc[0] = pair_tile(t, n, run, tpp, TILE, split);
+    __syncwarp();
+    prepare_tile(src, desc[0], in_buf[0], &bar[0], lane);
   }
   __syncthreads();
   bool ok = true;
@@ -424,29 +503,20 @@ __global__ void __launch_bounds__(NT, 4) merge_keys_tma_kernel(
       ok = false;
       break;
     }
-    // all threads are past the previous tile: its buffer and descriptor are free
-    if (tid == 0 && tn < num_tiles) {
-      desc[b ^ 1] = pair_tile(tn, n, run, tpp, TILE, split);
-      issue_tile_loads(src, n_al, desc[b ^ 1], in_buf[b ^ 1], &bar[b ^ 1]);
+    // every thread is past the previous tile: its buffer and descriptor are free
+    if (warp == 0 && tn < num_tiles) {
+      if (lane == 0) desc[b ^ 1] = pair_tile(tn, n, run, tpp, TILE, split);
+      __syncwarp();
+      prepare_tile(src, desc[b ^ 1], in_buf[b ^ 1], &bar[b ^ 1], lane);
     }
     const PairTile g = desc[b];
     const SmemSlices l = smem_slices(g);
-    uint32_t *s = in_buf[b];
-    if (g.a_off + g.na > n_al || g.b_off + g.nb > n_al) {   // uniform: the array's last tile
-      if (tid < 4) {
-        const int64_t ia = (g.a_off > n_al ? g.a_off : n_al) + tid;
-        if (ia < g.a_off + g.na) s[l.sh_a + (int)(ia - g.a_off)] = src[ia];
-        const int64_t ib = (g.b_off > n_al ? g.b_off : n_al) + tid;
-        if (ib < g.b_off + g.nb) s[l.base_b + l.sh_b + (int)(ib - g.b_off)] = src[ib];
-        fence_proxy_async_smem();   // ordered before later bulk copies into this buffer
-      }
-      __syncthreads();
-    }
+    const uint32_t *s = in_buf[b];
     const int a0 = l.sh_a, b0 = l.base_b + l.sh_b;
     const int diag = tid * VT < g.count ? tid * VT : g.count;
     const int ai = merge_path_plain(s, a0, g.na, b0, g.nb, diag);
     uint32_t o[VT];
-    serial_merge_plain<VT>(s, a0 + ai, a0 + g.na, b0 + diag - ai, b0 + g.nb, o);
+    serial_merge_sentinel<VT>(s, a0 + ai, b0 + diag - ai, o);
     // this warp's slice of the output: stage, then one bulk store by lane 0
     const int w0 = warp * WOUT;
     const int wcount = g.count - w0 < WOUT ? g.count - w0 : WOUT;
@@ -462,6 +532,11 @@ __global__ void __launch_bounds__(NT, 4) merge_keys_tma_kernel(
     }
     fence_proxy_async_smem();
     __syncwarp();
+    if (samp && wcount > 0) {   // every SAMPLE-th output of the pass, for the next partition
+      const int64_t gb = g.out0 + w0;
+      const int e = (int)((SAMPLE - (gb & (SAMPLE - 1))) & (SAMPLE - 1)) + SAMPLE * lane;
+      if (e < wcount) store_keep_in_l2(samp + (gb + e) / SAMPLE, wout[e]);
+    }
     if (wcount > 0) {
       const int body = wcount & ~3;
       if (lane == 0 && body) {
@@ -489,6 +564,11 @@ constexpr int PMERGE_VT = 16;
 constexpr int TMA_MERGE_NT = 128;   // persistent merge pass: 128 threads x 31 = 3968 outputs
 constexpr int TMA_MERGE_VT = 31;
 constexpr int TMA_MERGE_TILE = TMA_MERGE_NT * TMA_MERGE_VT;
+
+// dynamic shared memory of merge_keys_tma_kernel: two input buffers and the
+// output staging area (IN_LEN words each input; TILE words out)
+constexpr size_t TMA_MERGE_SMEM =
+    sizeof(uint32_t) * (2 * ((TMA_MERGE_TILE + 2 * 32 + 16) & ~3) + TMA_MERGE_TILE);
 
 constexpr int KEYS_SORT_TILE = KEYS_SORT_NT * 16;
 constexpr int PAIRS_SORT_TILE = PAIRS_SORT_NT * 16;
@@ -534,9 +614,10 @@ Plan make_plan(int kind, uint64_t n) {
   p.keys_off = 256;
   p.vals_off = p.keys_off + kb;
   p.split_off = pairs ? p.vals_off + kb : p.keys_off + kb;
+  p.samp_off = p.split_off + align_up((size_t)(max_tiles + 1) * sizeof(int64_t), 256);
   p.total = p.merge_passes == 0
                 ? 0
-                : p.split_off + align_up((size_t)(max_tiles + 1) * sizeof(int64_t), 256);
+                : p.samp_off + (pairs ? 0 : align_up((size_t)(n / SAMPLE + 2) * 4, 256));
   return p;
 }
 
@@ -550,9 +631,9 @@ static int launch_status(const char *what) {
 // ---- template dispatch (key type and "last pass" are compile-time) -------
 
 static void launch_tile_sort_keys(const uint32_t *in, uint32_t *out, int64_t n, int dt,
-                                  bool final_pass, unsigned grid, cudaStream_t st) {
+                                  bool final_pass, unsigned grid, uint32_t *samp, cudaStream_t st) {
 #define NSORT_TSK(DT, FIN) \
-  tile_sort_keys_kernel<KEYS_SORT_NT, DT, FIN><<<grid, KEYS_SORT_NT, 0, st>>>(in, out, n)
+  tile_sort_keys_kernel<KEYS_SORT_NT, DT, FIN><<<grid, KEYS_SORT_NT, 0, st>>>(in, out, n, samp)
   if (dt == DT_U32) { if (final_pass) NSORT_TSK(DT_U32, true); else NSORT_TSK(DT_U32, false); }
   else if (dt == DT_I32) { if (final_pass) NSORT_TSK(DT_I32, true); else NSORT_TSK(DT_I32, false); }
   else { if (final_pass) NSORT_TSK(DT_F32, true); else NSORT_TSK(DT_F32, false); }
@@ -630,35 +711,41 @@ static int tma_merge_grid(int64_t tiles) {
   if (g == 0) {
     int sms = 0, occ = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // prefer shared memory over L1: the pass keeps its data in shared memory
-    cudaFuncSetAttribute(merge_keys_tma_kernel<TMA_MERGE_NT, TMA_MERGE_VT, DT_U32>,
-                         cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    cudaFuncSetAttribute(merge_keys_tma_kernel<TMA_MERGE_NT, TMA_MERGE_VT, DT_I32>,
-                         cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    cudaFuncSetAttribute(merge_keys_tma_kernel<TMA_MERGE_NT, TMA_MERGE_VT, DT_F32>,
-                         cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    // opt in to the dynamic shared memory, and prefer shared memory over L1
+    const void *fns[3] = {(const void *)merge_keys_tma_kernel<TMA_MERGE_NT, TMA_MERGE_VT, DT_U32>,
+                          (const void *)merge_keys_tma_kernel<TMA_MERGE_NT, TMA_MERGE_VT, DT_I32>,
+                          (const void *)merge_keys_tma_kernel<TMA_MERGE_NT, TMA_MERGE_VT, DT_F32>};
+    for (const void *f : fns) {
+      cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TMA_MERGE_SMEM);
+      cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    }
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &occ, merge_keys_tma_kernel<TMA_MERGE_NT, TMA_MERGE_VT, DT_U32>, TMA_MERGE_NT, 0);
+        &occ, merge_keys_tma_kernel<TMA_MERGE_NT, TMA_MERGE_VT, DT_U32>, TMA_MERGE_NT,
+        TMA_MERGE_SMEM);
     g = (sms > 0 ? sms : 1) * (occ > 0 ? occ : 1);
     if (dev < 64) cached[dev].store(g);
   }
   return (int)(tiles < g ? tiles : g);
 }
 
+// samp_in: samples of src (from the previous stage); samp_out: where this
+// pass writes the samples of dst (nullptr for the last pass).
 static void launch_merge_keys_tma(const uint32_t *src, uint32_t *dst, int64_t n, int64_t run,
-                                  int64_t *split, int *status, int dt_out, cudaStream_t st) {
+                                  int64_t *split, int *status, int dt_out, const uint32_t *samp_in,
+                                  uint32_t *samp_out, cudaStream_t st) {
   int64_t tpp = 0;
   const int64_t tiles = pair_tiles(n, run, TMA_MERGE_TILE, &tpp);
   {
     TraceScope tr(TK_PARTITION, st);
-    partition_pairs_kernel<<<(unsigned)((tiles + 255) / 256), 256, 0, st>>>(
-        src, n, run, tpp, TMA_MERGE_TILE, tiles, split);
+    partition_sampled_kernel<<<(unsigned)((tiles + 255) / 256), 256, 0, st>>>(
+        src, samp_in, n, run, tpp, TMA_MERGE_TILE, tiles, split);
   }
   const unsigned grid = (unsigned)tma_merge_grid(tiles);
   TraceScope tr(TK_MERGE_KEYS, st);
 #define NSORT_MKT(DT)                                                                   \
-  merge_keys_tma_kernel<TMA_MERGE_NT, TMA_MERGE_VT, DT><<<grid, TMA_MERGE_NT, 0, st>>>( \
-      src, dst, n, run, tpp, tiles, split, status)
+  merge_keys_tma_kernel<TMA_MERGE_NT, TMA_MERGE_VT, DT>                                   \
+      <<<grid, TMA_MERGE_NT, TMA_MERGE_SMEM, st>>>(src, dst, n, run, tpp, tiles, split, status, \
+                                                   samp_out)
   if (dt_out == DT_U32) NSORT_MKT(DT_U32);
   else if (dt_out == DT_I32) NSORT_MKT(DT_I32);
   else NSORT_MKT(DT_F32);
@@ -674,6 +761,7 @@ int sort_keys_impl(const uint32_t *in, uint32_t *out, int64_t n, int dt, void *t
   uint32_t *bufs[2] = {out, p.merge_passes ? reinterpret_cast<uint32_t *>(t + p.keys_off) : nullptr};
   int64_t *split = p.merge_passes ? reinterpret_cast<int64_t *>(t + p.split_off) : nullptr;
   int *status = p.merge_passes ? reinterpret_cast<int *>(t + p.status_off) : nullptr;
+  uint32_t *samp = p.merge_passes ? reinterpret_cast<uint32_t *>(t + p.samp_off) : nullptr;
   if (status && cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess)
     return launch_status("cudaMemsetAsync");
   // the bulk-copy merge pass needs 16-byte aligned ping-pong buffers (the
@@ -683,14 +771,18 @@ int sort_keys_impl(const uint32_t *in, uint32_t *out, int64_t n, int dt, void *t
   const int64_t tiles = (n + p.sort_tile - 1) / p.sort_tile;
   {
     TraceScope tr(TK_TILE_SORT_KEYS, st);
-    launch_tile_sort_keys(in, bufs[cur], n, dt, p.merge_passes == 0, (unsigned)tiles, st);
+    launch_tile_sort_keys(in, bufs[cur], n, dt, p.merge_passes == 0, (unsigned)tiles,
+                          tma ? samp : nullptr, st);
   }
   int rc = launch_status("tile_sort_keys");
   for (int pass = 0; rc == NSORT_OK && pass < p.merge_passes; ++pass) {
     const int64_t run = (int64_t)p.sort_tile << pass;
     const int dt_out = pass == p.merge_passes - 1 ? dt : DT_U32;
     if (tma) {
-      launch_merge_keys_tma(bufs[cur], bufs[cur ^ 1], n, run, split, status, dt_out, st);
+      // the partition reads the samples of this pass's input before the
+      // merge overwrites them with the samples of its output
+      launch_merge_keys_tma(bufs[cur], bufs[cur ^ 1], n, run, split, status, dt_out, samp,
+                            pass == p.merge_passes - 1 ? nullptr : samp, st);
     } else {
       {
         TraceScope tr(TK_PARTITION, st);

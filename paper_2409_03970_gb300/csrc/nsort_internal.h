@@ -25,6 +25,7 @@ struct Plan {
   size_t keys_off = 0;       // ping-pong key buffer
   size_t vals_off = 0;       // ping-pong value buffer (pairs)
   size_t split_off = 0;      // int64 merge-path splitters, one per merge tile
+  size_t samp_off = 0;       // keys: every 64th key of the last stage's output
   size_t total = 0;          // bytes of scratch (0 when one tile holds everything)
 };
 

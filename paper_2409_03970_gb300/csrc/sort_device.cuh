@@ -275,6 +275,29 @@ __device__ __forceinline__ void serial_merge_plain(const uint32_t *s, int a, int
   }
 }
 
+// Keys-only serial merge without bounds checks: both runs must be followed
+// in shared memory by at least VT copies of the largest key (0xFFFFFFFF).
+// Once a run is exhausted its head reads as the largest key, so the other
+// run is taken; when both heads are the largest key, either may be output —
+// keys only, so equal keys are the same bits and the outputs are exact.
+template <int VT>
+__device__ __forceinline__ void serial_merge_sentinel(const uint32_t *s, int a, int b,
+                                                      uint32_t (&out)[VT]) {
+  uint32_t ka = s[a];
+  uint32_t kb = s[b];
+#pragma unroll
+  for (int k = 0; k < VT; ++k) {
+    const bool take_a = ka <= kb;
+    out[k] = take_a ? ka : kb;
+    const int nx = (take_a ? a : b) + 1;
+    const uint32_t kn = s[nx];
+    a = take_a ? nx : a;
+    b = take_a ? b : nx;
+    ka = take_a ? kn : ka;
+    kb = take_a ? kb : kn;
+  }
+}
+
 // ---- serial merge (the serial half of the hybrid merger) ----------------
 // Produces VT outputs of the stable merge of s[a, a_end) and s[b, b_end)
 // (element indices, padded layout) into out[].  Branch-free: one compare,

@@ -97,4 +97,13 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// Store that asks L2 to keep the line (evict-last priority): for the small
+// sample arrays that the next partition kernel reads.
+__device__ __forceinline__ void store_keep_in_l2(uint32_t *p, uint32_t v) {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  asm volatile("st.global.L2::cache_hint.b32 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(pol)
+               : "memory");
+}
+
 }  // namespace nsort

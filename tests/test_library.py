@@ -60,9 +60,10 @@ def test_temp_bytes(lib):
     assert nsort.nsort_temp_bytes(nsort.KIND_KEYS, st) == 0          # one tile: no scratch
     n = 1 << 20
     tb = nsort.nsort_temp_bytes(nsort.KIND_KEYS, n)
-    # one ping-pong copy, the status word and one splitter per merge tile of the
-    # pass with the most tiles (tiles never span two run pairs)
-    assert 4 * n <= tb <= 4 * n + 8 * (n // mt + n // (2 * st) + 3) + 1024
+    # one ping-pong copy, the status word, one splitter per merge tile of the
+    # pass with the most tiles (tiles never span two run pairs) and every
+    # 64th key of a pass's output
+    assert 4 * n <= tb <= 4 * n + 8 * (n // mt + n // (2 * st) + 3) + 4 * (n // 64 + 2) + 1280
     tp = nsort.nsort_temp_bytes(nsort.KIND_PAIRS, n)
     _, pst, pmt = nsort.nsort_plan(nsort.KIND_PAIRS, n)
     assert 8 * n <= tp <= 8 * n + 8 * (n // pmt + n // (2 * pst) + 3) + 1024
