@@ -317,6 +317,29 @@ struct PairTile {
   int na, nb, count;
 };
 
+// Geometry of tile t from its start splitter s0 and the next tile's s1
+// (s1 is ignored when the tile ends its pair).
+__device__ __forceinline__ PairTile pair_tile_from(int64_t t, int64_t n, int64_t run, int64_t tpp,
+                                                   int tile, int64_t s0, int64_t s1) {
+  PairTile g;
+  const int64_t pair = t / tpp;
+  const int64_t j = t - pair * tpp;
+  const int64_t pair0 = pair * 2 * run;
+  const int64_t la = n - pair0 < run ? n - pair0 : run;
+  const int64_t rest = n - pair0 - run;
+  const int64_t lb = rest <= 0 ? 0 : (rest < run ? rest : run);
+  const int64_t pend = pair0 + la + lb;
+  g.out0 = pair0 + j * tile;
+  const int64_t out1 = g.out0 + tile < pend ? g.out0 + tile : pend;
+  const int64_t a_end = out1 == pend ? la : s1;
+  g.a_off = pair0 + s0;
+  g.b_off = pair0 + la + (g.out0 - pair0 - s0);
+  g.na = (int)(a_end - s0);
+  g.count = (int)(out1 - g.out0);
+  g.nb = g.count - g.na;
+  return g;
+}
+
 __device__ __forceinline__ PairTile pair_tile(int64_t t, int64_t n, int64_t run, int64_t tpp,
                                               int tile, const int64_t *split) {
   PairTile g;
@@ -415,46 +438,36 @@ __device__ __forceinline__ SmemSlices smem_slices(const PairTile &g) {
   return l;
 }
 
-// Prepares tile g in buffer buf (run by the 32 lanes of warp 0, into a
-// buffer no other thread is using): bulk copies of the 16-byte-aligned
-// bodies of both slices (rounded down at the end, so the copies never write
-// past a slice), ordinary loads of the ragged ends (at most 3 elements per
-// slice), and SENT largest-key sentinels after each slice.  The plain writes
-// and the bulk copies touch disjoint shared memory; the plain writes are
-// ordered before the bulk copies that later reuse this buffer by the proxy
-// fence, and before the merge by the CTA barrier that follows the wait.
-__device__ __forceinline__ void prepare_tile(const uint32_t *__restrict__ src, const PairTile &g,
-                                             uint32_t *buf, uint64_t *bar, int lane) {
+// Issues the bulk copies of tile g into buf (lane 0 of warp 0, into a
+// buffer no thread is reading).  Each slice's window is rounded out to
+// 16-byte boundaries, so up to 3 elements past a slice land in its sentinel
+// area (the warps overwrite them with sentinels before merging); windows
+// are clipped at n_al = n & ~3, past which the warps load the at most 3
+// remaining elements themselves.
+__device__ __forceinline__ void issue_tile(const uint32_t *__restrict__ src, int64_t n_al,
+                                           const PairTile &g, uint32_t *buf, uint64_t *bar) {
   const SmemSlices l = smem_slices(g);
-  const int a0 = l.sh_a, b0 = l.base_b + l.sh_b;
-  const int64_t aw0 = g.a_off & ~int64_t(3), aw1 = (g.a_off + g.na) & ~int64_t(3);
-  const int64_t bw0 = g.b_off & ~int64_t(3), bw1 = (g.b_off + g.nb) & ~int64_t(3);
-  if (lane < 3) {
-    const int64_t i = aw1 + lane;
-    if (i >= g.a_off && i < g.a_off + g.na) buf[a0 + (int)(i - g.a_off)] = __ldg(src + i);
-  } else if (lane < 6) {
-    const int64_t i = bw1 + (lane - 3);
-    if (i >= g.b_off && i < g.b_off + g.nb) buf[b0 + (int)(i - g.b_off)] = __ldg(src + i);
-  }
-  static_assert(SENT == 32, "one sentinel per lane and slice");
-  buf[a0 + g.na + lane] = 0xFFFFFFFFu;
-  buf[b0 + g.nb + lane] = 0xFFFFFFFFu;
-  fence_proxy_async_smem();
-  __syncwarp();
-  if (lane == 0) {
-    const uint32_t bytes_a = aw1 > aw0 ? (uint32_t)((aw1 - aw0) * 4) : 0u;
-    const uint32_t bytes_b = bw1 > bw0 ? (uint32_t)((bw1 - bw0) * 4) : 0u;
-    mbar_arrive_expect_tx(bar, bytes_a + bytes_b);
-    if (bytes_a) bulk_load(buf, src + aw0, bytes_a, bar);
-    if (bytes_b) bulk_load(buf + l.base_b, src + bw0, bytes_b, bar);
-  }
+  const int64_t aw0 = g.a_off & ~int64_t(3);
+  int64_t aw1 = (g.a_off + g.na + 3) & ~int64_t(3);
+  const int64_t bw0 = g.b_off & ~int64_t(3);
+  int64_t bw1 = (g.b_off + g.nb + 3) & ~int64_t(3);
+  aw1 = aw1 < n_al ? aw1 : n_al;
+  bw1 = bw1 < n_al ? bw1 : n_al;
+  const uint32_t bytes_a = (g.na > 0 && aw1 > aw0) ? (uint32_t)((aw1 - aw0) * 4) : 0u;
+  const uint32_t bytes_b = (g.nb > 0 && bw1 > bw0) ? (uint32_t)((bw1 - bw0) * 4) : 0u;
+  mbar_arrive_expect_tx(bar, bytes_a + bytes_b);
+  if (bytes_a) bulk_load(buf, src + aw0, bytes_a, bar);
+  if (bytes_b) bulk_load(buf + l.base_b, src + bw0, bytes_b, bar);
 }
 
 // Per tile, one CTA-wide barrier: after it, every thread is done with the
-// previous tile, so warp 0 can prepare the next tile in that buffer while
-// the CTA merges this one.  Each warp's outputs are contiguous (32 * VT
-// keys), so each warp stages and bulk-stores its own part with warp-level
-// synchronisation only.
+// previous tile, so lane 0 of warp 0 can reuse that buffer for the next
+// tile's copies while the CTA merges this one.  Every warp writes the
+// sentinels (and, at the array's end, the last elements) it will read
+// itself, so no other barrier is needed; each warp's outputs are contiguous
+// (32 * VT keys), so each warp stages and bulk-stores its own part with
+// warp-level synchronisation only.  Lane 0 of warp 0 loads the splitters of
+// the tile after next one iteration early, off the critical path.
 template <int NT, int VT, int DT_OUT>
 __global__ void __launch_bounds__(NT, 4) merge_keys_tma_kernel(
     const uint32_t *__restrict__ src, uint32_t *__restrict__ dst, int64_t n, int64_t run,
@@ -465,35 +478,41 @@ __global__ void __launch_bounds__(NT, 4) merge_keys_tma_kernel(
   // A window + sentinels, B window + sentinels, rounding slack
   constexpr int IN_LEN = (TILE + 2 * SENT + 16) & ~3;
   static_assert(SENT >= VT + 1, "each run needs VT sentinels past its end");
+  static_assert(SENT == 32, "one sentinel per lane and slice");
   static_assert(WOUT % 4 == 0, "warp output slices must be 16-byte multiples");
   static_assert(WOUT <= 32 * SAMPLE, "one sample per lane and warp slice");
-  // dynamic shared memory: [in_buf 0][in_buf 1][out_buf] (tma_merge_smem_bytes)
+  // dynamic shared memory: [in_buf 0][in_buf 1][out_buf] (TMA_MERGE_SMEM)
   extern __shared__ __align__(128) unsigned char tma_smem[];
   uint32_t(*in_buf)[IN_LEN] = reinterpret_cast<uint32_t(*)[IN_LEN]>(tma_smem);
   uint32_t *out_buf = reinterpret_cast<uint32_t *>(tma_smem) + 2 * IN_LEN;
   __shared__ __align__(8) uint64_t bar[2];
-  __shared__ PairTile desc[2];   // geometry of the tile in each buffer, written by warp 0
+  __shared__ PairTile desc[2];   // geometry of the tile in each buffer, written by thread 0
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int warp = tid >> 5;
+  const int64_t n_al = n & ~int64_t(3);
+  const int64_t G = gridDim.x;
   int64_t t = blockIdx.x;
+  int64_t pf0 = 0, pf1 = 0;   // thread 0: splitters of tile t + G
   if (tid == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     fence_mbar_init();
-  }
-  __syncthreads();
-  if (warp == 0 && t < num_tiles) {
-    if (lane == 0) desc[0] = pair_tile(t, n, run, tpp, TILE, split);
-    __syncwarp();
-    prepare_tile(src, desc[0], in_buf[0], &bar[0], lane);
+    if (t < num_tiles) {
+      desc[0] = pair_tile(t, n, run, tpp, TILE, split);
+      issue_tile(src, n_al, desc[0], in_buf[0], &bar[0]);
+    }
+    if (t + G < num_tiles) {
+      pf0 = split[t + G];
+      pf1 = t + G + 1 < num_tiles ? split[t + G + 1] : 0;
+    }
   }
   __syncthreads();
   bool ok = true;
   uint32_t *wout = out_buf + warp * WOUT;
-  for (int it = 0; t < num_tiles; ++it, t += gridDim.x) {
+  for (int it = 0; t < num_tiles; ++it, t += G) {
     const int b = it & 1;
-    const int64_t tn = t + gridDim.x;
+    const int64_t tn = t + G;
     const uint32_t parity = (uint32_t)((it >> 1) & 1);
     const bool got = mbar_wait(&bar[b], parity);
     if (!__syncthreads_and(got)) {
@@ -504,15 +523,33 @@ __global__ void __launch_bounds__(NT, 4) merge_keys_tma_kernel(
       break;
     }
     // every thread is past the previous tile: its buffer and descriptor are free
-    if (warp == 0 && tn < num_tiles) {
-      if (lane == 0) desc[b ^ 1] = pair_tile(tn, n, run, tpp, TILE, split);
-      __syncwarp();
-      prepare_tile(src, desc[b ^ 1], in_buf[b ^ 1], &bar[b ^ 1], lane);
+    if (tid == 0 && tn < num_tiles) {
+      desc[b ^ 1] = pair_tile_from(tn, n, run, tpp, TILE, pf0, pf1);
+      issue_tile(src, n_al, desc[b ^ 1], in_buf[b ^ 1], &bar[b ^ 1]);
+      const int64_t tp = tn + G;
+      if (tp < num_tiles) {
+        pf0 = split[tp];
+        pf1 = tp + 1 < num_tiles ? split[tp + 1] : 0;
+      }
     }
     const PairTile g = desc[b];
     const SmemSlices l = smem_slices(g);
-    const uint32_t *s = in_buf[b];
+    uint32_t *s = in_buf[b];
     const int a0 = l.sh_a, b0 = l.base_b + l.sh_b;
+    // this warp's own sentinels and array-end elements (same values in every warp)
+    if (g.a_off + g.na > n_al || g.b_off + g.nb > n_al) {
+      if (lane < 3) {
+        const int64_t i = (g.a_off > n_al ? g.a_off : n_al) + lane;
+        if (i < g.a_off + g.na) s[a0 + (int)(i - g.a_off)] = __ldg(src + i);
+      } else if (lane < 6) {
+        const int64_t i = (g.b_off > n_al ? g.b_off : n_al) + (lane - 3);
+        if (i < g.b_off + g.nb) s[b0 + (int)(i - g.b_off)] = __ldg(src + i);
+      }
+    }
+    s[a0 + g.na + lane] = 0xFFFFFFFFu;
+    s[b0 + g.nb + lane] = 0xFFFFFFFFu;
+    fence_proxy_async_smem();   // ordered before later bulk copies into this buffer
+    __syncwarp();
     const int diag = tid * VT < g.count ? tid * VT : g.count;
     const int ai = merge_path_plain(s, a0, g.na, b0, g.nb, diag);
     uint32_t o[VT];
