@@ -472,7 +472,7 @@ template <int NT, int VT, int DT_OUT>
 __global__ void __launch_bounds__(NT, 4) merge_keys_tma_kernel(
     const uint32_t *__restrict__ src, uint32_t *__restrict__ dst, int64_t n, int64_t run,
     int64_t tpp, int64_t num_tiles, const int64_t *__restrict__ split, int *status,
-    uint32_t *samp) {
+    uint32_t *samp, int reverse) {
   constexpr int TILE = NT * VT;
   constexpr int WOUT = 32 * VT;                       // outputs per warp
   // A window + sentinels, B window + sentinels, rounding slack
@@ -493,18 +493,23 @@ __global__ void __launch_bounds__(NT, 4) merge_keys_tma_kernel(
   const int64_t n_al = n & ~int64_t(3);
   const int64_t G = gridDim.x;
   int64_t t = blockIdx.x;
-  int64_t pf0 = 0, pf1 = 0;   // thread 0: splitters of tile t + G
+  // loop index i -> tile: ascending, or descending when `reverse` (passes
+  // alternate direction so that each pass starts where the previous one
+  // ended, on data still in L2)
+  auto tile_of = [&](int64_t i) { return reverse ? num_tiles - 1 - i : i; };
+  int64_t pf0 = 0, pf1 = 0;   // thread 0: splitters of loop index t + G
   if (tid == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     fence_mbar_init();
     if (t < num_tiles) {
-      desc[0] = pair_tile(t, n, run, tpp, TILE, split);
+      desc[0] = pair_tile(tile_of(t), n, run, tpp, TILE, split);
       issue_tile(src, n_al, desc[0], in_buf[0], &bar[0]);
     }
     if (t + G < num_tiles) {
-      pf0 = split[t + G];
-      pf1 = t + G + 1 < num_tiles ? split[t + G + 1] : 0;
+      const int64_t u = tile_of(t + G);
+      pf0 = split[u];
+      pf1 = u + 1 < num_tiles ? split[u + 1] : 0;
     }
   }
   __syncthreads();
@@ -524,12 +529,13 @@ __global__ void __launch_bounds__(NT, 4) merge_keys_tma_kernel(
     }
     // every thread is past the previous tile: its buffer and descriptor are free
     if (tid == 0 && tn < num_tiles) {
-      desc[b ^ 1] = pair_tile_from(tn, n, run, tpp, TILE, pf0, pf1);
+      desc[b ^ 1] = pair_tile_from(tile_of(tn), n, run, tpp, TILE, pf0, pf1);
       issue_tile(src, n_al, desc[b ^ 1], in_buf[b ^ 1], &bar[b ^ 1]);
       const int64_t tp = tn + G;
       if (tp < num_tiles) {
-        pf0 = split[tp];
-        pf1 = tp + 1 < num_tiles ? split[tp + 1] : 0;
+        const int64_t u = tile_of(tp);
+        pf0 = split[u];
+        pf1 = u + 1 < num_tiles ? split[u + 1] : 0;
       }
     }
     const PairTile g = desc[b];
@@ -769,7 +775,7 @@ static int tma_merge_grid(int64_t tiles) {
 // pass writes the samples of dst (nullptr for the last pass).
 static void launch_merge_keys_tma(const uint32_t *src, uint32_t *dst, int64_t n, int64_t run,
                                   int64_t *split, int *status, int dt_out, const uint32_t *samp_in,
-                                  uint32_t *samp_out, cudaStream_t st) {
+                                  uint32_t *samp_out, int reverse, cudaStream_t st) {
   int64_t tpp = 0;
   const int64_t tiles = pair_tiles(n, run, TMA_MERGE_TILE, &tpp);
   {
@@ -782,7 +788,7 @@ static void launch_merge_keys_tma(const uint32_t *src, uint32_t *dst, int64_t n,
 #define NSORT_MKT(DT)                                                                   \
   merge_keys_tma_kernel<TMA_MERGE_NT, TMA_MERGE_VT, DT>                                   \
       <<<grid, TMA_MERGE_NT, TMA_MERGE_SMEM, st>>>(src, dst, n, run, tpp, tiles, split, status, \
-                                                   samp_out)
+                                                   samp_out, reverse)
   if (dt_out == DT_U32) NSORT_MKT(DT_U32);
   else if (dt_out == DT_I32) NSORT_MKT(DT_I32);
   else NSORT_MKT(DT_F32);
@@ -818,8 +824,9 @@ int sort_keys_impl(const uint32_t *in, uint32_t *out, int64_t n, int dt, void *t
     if (tma) {
       // the partition reads the samples of this pass's input before the
       // merge overwrites them with the samples of its output
+      // the tile sort writes low to high; passes then alternate direction
       launch_merge_keys_tma(bufs[cur], bufs[cur ^ 1], n, run, split, status, dt_out, samp,
-                            pass == p.merge_passes - 1 ? nullptr : samp, st);
+                            pass == p.merge_passes - 1 ? nullptr : samp, (pass & 1) == 0, st);
     } else {
       {
         TraceScope tr(TK_PARTITION, st);
