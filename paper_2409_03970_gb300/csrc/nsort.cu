@@ -104,7 +104,8 @@ template <int NT, int DT, bool FINAL>
 __global__ void __launch_bounds__(NT) tile_sort_keys_kernel(const uint32_t *in, uint32_t *out,
                                                             int64_t n, uint32_t *samp) {
   constexpr int TILE = NT * 16;
-  __shared__ uint32_t s[merge_smem_len<uint32_t>(TILE, 16)];
+  extern __shared__ __align__(16) unsigned char tile_smem[];   // merge_smem_len(TILE, 16) words
+  uint32_t *s = reinterpret_cast<uint32_t *>(tile_smem);
   const int tid = threadIdx.x;
   const int64_t base = (int64_t)blockIdx.x * TILE;
   const int count = (int)(n - base < TILE ? n - base : TILE);
@@ -614,6 +615,7 @@ constexpr size_t TMA_MERGE_SMEM =
     sizeof(uint32_t) * (2 * ((TMA_MERGE_TILE + 2 * 32 + 16) & ~3) + TMA_MERGE_TILE);
 
 constexpr int KEYS_SORT_TILE = KEYS_SORT_NT * 16;
+constexpr size_t KEYS_SORT_SMEM = sizeof(uint32_t) * merge_smem_len<uint32_t>(KEYS_SORT_TILE, 16);
 constexpr int PAIRS_SORT_TILE = PAIRS_SORT_NT * 16;
 constexpr int MERGE_TILE = MERGE_NT * MERGE_VT;
 constexpr int PMERGE_TILE = PMERGE_NT * PMERGE_VT;
@@ -673,10 +675,30 @@ static int launch_status(const char *what) {
 
 // ---- template dispatch (key type and "last pass" are compile-time) -------
 
+template <int DT, bool FIN>
+static void keys_sort_smem_attr() {
+  cudaFuncSetAttribute(tile_sort_keys_kernel<KEYS_SORT_NT, DT, FIN>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)KEYS_SORT_SMEM);
+}
+
 static void launch_tile_sort_keys(const uint32_t *in, uint32_t *out, int64_t n, int dt,
                                   bool final_pass, unsigned grid, uint32_t *samp, cudaStream_t st) {
-#define NSORT_TSK(DT, FIN) \
-  tile_sort_keys_kernel<KEYS_SORT_NT, DT, FIN><<<grid, KEYS_SORT_NT, 0, st>>>(in, out, n, samp)
+  static std::atomic<uint64_t> done_mask{0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const uint64_t bit = dev < 64 ? (uint64_t(1) << dev) : 0;
+  if (!bit || !(done_mask.load() & bit)) {   // opt in to the dynamic shared memory, once per device
+    keys_sort_smem_attr<DT_U32, false>();
+    keys_sort_smem_attr<DT_U32, true>();
+    keys_sort_smem_attr<DT_I32, false>();
+    keys_sort_smem_attr<DT_I32, true>();
+    keys_sort_smem_attr<DT_F32, false>();
+    keys_sort_smem_attr<DT_F32, true>();
+    done_mask.fetch_or(bit);
+  }
+#define NSORT_TSK(DT, FIN)                                                        \
+  tile_sort_keys_kernel<KEYS_SORT_NT, DT, FIN><<<grid, KEYS_SORT_NT, KEYS_SORT_SMEM, st>>>( \
+      in, out, n, samp)
   if (dt == DT_U32) { if (final_pass) NSORT_TSK(DT_U32, true); else NSORT_TSK(DT_U32, false); }
   else if (dt == DT_I32) { if (final_pass) NSORT_TSK(DT_I32, true); else NSORT_TSK(DT_I32, false); }
   else { if (final_pass) NSORT_TSK(DT_F32, true); else NSORT_TSK(DT_F32, false); }

@@ -53,7 +53,8 @@ def gpu_pairs(ns, k, v, dt, inplace=False):
 
 
 SIZES = [0, 1, 2, 3, 15, 16, 17, 511, 512, 513, 4095, 4096, 4097, 8191, 8192, 8193,
-         3 * 8192 + 5, 65536 + 1, 100_003, 1 << 20, (1 << 20) + 12345]
+         16383, 16384, 16385, 3 * 8192 + 5, 3 * 16384 + 7, 65536 + 1, 100_003, 1 << 20,
+         (1 << 20) + 12345]
 
 
 @pytest.mark.parametrize("n", SIZES)
