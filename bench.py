@@ -17,6 +17,7 @@ host cores, on a bounded sample of the same workload each step.
 from __future__ import annotations
 
 import argparse
+import collections
 import glob
 import hashlib
 import json
@@ -305,6 +306,57 @@ def bench_e2e(nsort, torch, host_in, x, out, tmp, n, code, steps, world):
             "one_step_unpipelined_ms": serial_ms}
 
 
+def time_sort(nsort, torch, fn, reps: int = 5, warm: int = 2):
+    """Device time of fn() (one sort), median of `reps` after `warm` runs."""
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ts = []
+    for _ in range(reps):
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return float(np.median(ts))
+
+
+def bench_configs(nsort, torch):
+    """The other plain-sort configurations: 2^28 int32 / float32 keys over
+    several distributions, and 2^27 stable float32 key / uint32 value pairs
+    (Normal(0,1) with 0.1% IEEE specials, payload = index)."""
+    from paper_2409_03970_gb300 import inputs
+    n = 1 << 28
+    out = {}
+    tmp = nsort.scratch(nsort.KIND_KEYS, n)
+    ko = torch.empty(n, dtype=torch.int32, device="cuda")
+    for dt, dist in (("i32", "uniform"), ("f32", "uniform"), ("f32", "sorted"),
+                     ("f32", "reverse"), ("f32", "dup16")):
+        x = torch.from_numpy(inputs.keys(n, dt, dist, seed=0).view(np.int32)).cuda()
+        code = {"i32": nsort.I32, "f32": nsort.F32}[dt]
+        ms = time_sort(nsort, torch,
+                       lambda: nsort.nsort_keys(x, ko, n, code, tmp, tmp.numel()))
+        out[f"keys_{dt}_{dist}_2e28"] = {"ms": ms, "gkeys_s": n / ms / 1e6}
+        del x
+    del tmp, ko
+    torch.cuda.empty_cache()
+    m = 1 << 27
+    k, v = inputs.normal_pairs(m, seed=0)
+    kt = torch.from_numpy(k.view(np.int32)).cuda()
+    vt = torch.from_numpy(v.view(np.int32)).cuda()
+    del k, v
+    kout, vout = torch.empty_like(kt), torch.empty_like(vt)
+    tmp = nsort.scratch(nsort.KIND_PAIRS, m)
+    passes, _, _ = nsort.nsort_plan(nsort.KIND_PAIRS, m)
+    ms = time_sort(nsort, torch, lambda: nsort.nsort_pairs(kt, vt, kout, vout, m, nsort.F32, tmp,
+                                                           tmp.numel()))
+    out["pairs_f32_normal_specials_2e27"] = {
+        "ms": ms, "gpairs_s": m / ms / 1e6, "passes": passes,
+        "hbm_roofline_frac": passes * 16 * m / (ms / 1e3) / 1e9 / load_peaks()["hbm_gbs"]}
+    return out
+
+
 # ---- batched (segmented) and served measurements -----------------------------
 
 def bench_batched(nsort, torch, nseg: int, reps: int = 5):
@@ -401,6 +453,7 @@ def bench_served(nsort, torch, duration: float, rate: float = 2000.0, budget: in
     def run(streams_, batch_):
         count = state["count"]
         total_keys = state["total_keys"]
+        due_at = arrival[:count]
         srv = nsort.SortServer(0, budget, streams_, batch_)
         # warm-up: one request of each mode and a small batch
         for m in range(4):
@@ -413,17 +466,23 @@ def bench_served(nsort, torch, duration: float, rate: float = 2000.0, budget: in
         kb, vb = pool_k.data_ptr(), pool_v.data_ptr()
         ob, ovb = out_k.data_ptr(), out_v.data_ptr()
         tickets = []
+        inflight = collections.deque()   # (start, end, ticket) of output regions in use
         rpos = 0
         t0 = time.monotonic()
         for i in range(count):
             n = int(sizes[i])
             if rpos + n > ring:
                 rpos = 0
+            # an output region is reused only after the request writing it is done
+            # (a sort uses its output as working space); latency still counts from
+            # the scheduled arrival
+            while inflight and inflight[0][0] < rpos + n and inflight[0][1] > rpos:
+                srv.wait(inflight.popleft()[2], 600000)
             m = int(modes[i])
             kind = nsort.KIND_PAIRS if m == 3 else nsort.KIND_KEYS
             dt = [nsort.U32, nsort.I32, nsort.F32, nsort.F32][m]
             st = int(starts[i])
-            due = t0 + arrival[i]
+            due = t0 + due_at[i]
             while True:
                 d = due - time.monotonic()
                 if d <= 0:
@@ -433,6 +492,7 @@ def bench_served(nsort, torch, duration: float, rate: float = 2000.0, budget: in
             tickets.append(nsort.nsort_submit(srv.ctx, kind, dt, n, kb + 4 * st, ob + 4 * rpos,
                                               vb + 4 * st if m == 3 else None,
                                               ovb + 4 * rpos if m == 3 else None))
+            inflight.append((rpos, rpos + n, tickets[-1]))
             rpos = (rpos + n + 3) & ~3
         done_t = np.empty(count)
         batched = 0
@@ -444,7 +504,7 @@ def bench_served(nsort, torch, duration: float, rate: float = 2000.0, budget: in
             done_t[i] = tm["t_done"]
             batched += tm["batched"]
         srv.close()
-        lat = (done_t - (t0 + arrival)) * 1e3
+        lat = (done_t - (t0 + due_at)) * 1e3
         span = done_t.max() - t0
         return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "mean_ms": float(lat.mean()), "gkeys_s": total_keys / span / 1e9,
@@ -584,9 +644,11 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.dtype)
 
-    batched = served = None
+    batched = served = configs = None
     if rank == 0 and world == 1 and not args.no_extras:
         del x, out, tmp, host_in
+        torch.cuda.empty_cache()
+        configs = bench_configs(nsort, torch)
         torch.cuda.empty_cache()
         batched = bench_batched(nsort, torch, args.segments)
         torch.cuda.empty_cache()
@@ -613,6 +675,7 @@ def main():
             "kernels": {k: {"launches": v["launches"], "ms_per_launch": v["total_ms"] / v["launches"]}
                         for k, v in trace.items()},
             "clocks": clk,
+            "other_configs": configs,
             "batched": batched,
             "served": served,
         }

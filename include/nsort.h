@@ -30,6 +30,11 @@
  *  - in == out is allowed (in-place sort).  d_tmp must not overlap any
  *    input or output.  Pointers need only 4-byte alignment; 16-byte aligned
  *    buffers take the vectorised path.
+ *  - The output (and d_tmp) are working space until the call's work on the
+ *    stream is complete: other work must not read or write them meanwhile,
+ *    and concurrent calls must use disjoint buffers.  (If they do not, the
+ *    result is undefined but every kernel still stays inside its buffers:
+ *    tile geometry is clamped to the runs whatever the data.)
  *  - Calls are asynchronous on `stream` (a cudaStream_t; NULL = the legacy
  *    default stream) and return after enqueueing.  Return value: an
  *    nsort_status.  Argument errors are detected before any launch;

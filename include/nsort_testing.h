@@ -29,6 +29,16 @@ int nsort_policy_pick_batch(const uint64_t *tickets, const int *kinds, const int
 int nsort_policy_arena_replay(uint64_t capacity, const int64_t *ops, int nops,
                               int64_t *offsets);
 
+/* Runs the library's bounded waits (the mbarrier wait of the merge pass and
+ * the completion-counter wait of the segmented sort) on events that never
+ * happen, with a limit of limit_us microseconds each, in one small kernel on
+ * `stream`.  Both waits give up; the kernel records NSORT_ETIMEOUT in the
+ * status word of d_tmp (at least 512 bytes, 256-byte aligned) and returns
+ * normally, so nsort_device_status(d_tmp) reports NSORT_ETIMEOUT and the
+ * context stays usable.  This is how time-outs are tested without hanging
+ * or faulting a GPU.  Paper: none. */
+int nsort_selftest_wait(void *d_tmp, size_t tmp_bytes, uint32_t limit_us, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

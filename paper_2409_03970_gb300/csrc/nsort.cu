@@ -182,6 +182,21 @@ __global__ void __launch_bounds__(NT) tile_sort_pairs_kernel(const uint32_t *kin
   store_run<16, DT_U32>(vo, vout + base, count, full);
 }
 
+// Clamps a tile's A co-ranks so that both slices stay inside their runs and
+// add up to the tile: a0 in [max(0, d0 - lb), min(d0, la)] and a1 in
+// [max(a0, d1 - lb), min(la, a0 + d1 - d0)].  For sorted runs the splitters
+// already satisfy this; the clamps only matter when the runs are not what
+// the splitters were computed from (another kernel writing the buffers
+// during the sort), and then keep every index of the merge in range.
+__device__ __forceinline__ void clamp_coranks(int64_t la, int64_t lb, int64_t d0, int64_t d1,
+                                              int64_t &a0, int64_t &a1) {
+  const int64_t lo0 = d0 - lb > 0 ? d0 - lb : 0, hi0 = d0 < la ? d0 : la;
+  a0 = a0 < lo0 ? lo0 : (a0 > hi0 ? hi0 : a0);
+  int64_t lo1 = d1 - lb > a0 ? d1 - lb : a0;
+  int64_t hi1 = a0 + (d1 - d0) < la ? a0 + (d1 - d0) : la;
+  a1 = a1 < lo1 ? lo1 : (a1 > hi1 ? hi1 : a1);
+}
+
 // Which slices of the two input runs one merge CTA consumes.
 struct PassTile {
   int64_t out0;      // first output element of the tile
@@ -200,8 +215,9 @@ __device__ __forceinline__ PassTile pass_tile(int64_t n, int64_t run, int tile,
   const int64_t rest = n - pair0 - run;
   const int64_t lb = rest <= 0 ? 0 : (rest < run ? rest : run);
   const int64_t pair_end = pair0 + la + lb;
-  const int64_t a_end = out1 == pair_end ? la : split[blockIdx.x + 1];
-  const int64_t a_beg = split[blockIdx.x];
+  int64_t a_end = out1 == pair_end ? la : split[blockIdx.x + 1];
+  int64_t a_beg = split[blockIdx.x];
+  clamp_coranks(la, lb, g.out0 - pair0, out1 - pair0, a_beg, a_end);
   const int64_t b_beg = (g.out0 - pair0) - a_beg;
   const int64_t b_end = (out1 - pair0) - a_end;
   g.a_off = pair0 + a_beg;
@@ -332,32 +348,12 @@ __device__ __forceinline__ PairTile pair_tile_from(int64_t t, int64_t n, int64_t
   const int64_t pend = pair0 + la + lb;
   g.out0 = pair0 + j * tile;
   const int64_t out1 = g.out0 + tile < pend ? g.out0 + tile : pend;
-  const int64_t a_end = out1 == pend ? la : s1;
-  g.a_off = pair0 + s0;
-  g.b_off = pair0 + la + (g.out0 - pair0 - s0);
-  g.na = (int)(a_end - s0);
-  g.count = (int)(out1 - g.out0);
-  g.nb = g.count - g.na;
-  return g;
-}
-
-__device__ __forceinline__ PairTile pair_tile(int64_t t, int64_t n, int64_t run, int64_t tpp,
-                                              int tile, const int64_t *split) {
-  PairTile g;
-  const int64_t pair = t / tpp;
-  const int64_t j = t - pair * tpp;
-  const int64_t pair0 = pair * 2 * run;
-  const int64_t la = n - pair0 < run ? n - pair0 : run;
-  const int64_t rest = n - pair0 - run;
-  const int64_t lb = rest <= 0 ? 0 : (rest < run ? rest : run);
-  const int64_t pend = pair0 + la + lb;
-  g.out0 = pair0 + j * tile;
-  const int64_t out1 = g.out0 + tile < pend ? g.out0 + tile : pend;
-  const int64_t a_beg = split[t];
-  const int64_t a_end = out1 == pend ? la : split[t + 1];
-  g.a_off = pair0 + a_beg;
-  g.b_off = pair0 + la + (g.out0 - pair0 - a_beg);
-  g.na = (int)(a_end - a_beg);
+  int64_t a0 = s0;
+  int64_t a1 = out1 == pend ? la : s1;
+  clamp_coranks(la, lb, g.out0 - pair0, out1 - pair0, a0, a1);
+  g.a_off = pair0 + a0;
+  g.b_off = pair0 + la + (g.out0 - pair0 - a0);
+  g.na = (int)(a1 - a0);
   g.count = (int)(out1 - g.out0);
   g.nb = g.count - g.na;
   return g;
@@ -504,7 +500,9 @@ __global__ void __launch_bounds__(NT, 4) merge_keys_tma_kernel(
     mbar_init(&bar[1], 1);
     fence_mbar_init();
     if (t < num_tiles) {
-      desc[0] = pair_tile(tile_of(t), n, run, tpp, TILE, split);
+      const int64_t u = tile_of(t);
+      desc[0] = pair_tile_from(u, n, run, tpp, TILE, split[u],
+                               u + 1 < num_tiles ? split[u + 1] : 0);
       issue_tile(src, n_al, desc[0], in_buf[0], &bar[0]);
     }
     if (t + G < num_tiles) {

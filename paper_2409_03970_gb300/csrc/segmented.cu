@@ -32,6 +32,7 @@
 #include "nsort.h"
 #include "nsort_internal.h"
 #include "sort_device.cuh"
+#include "tma_device.cuh"
 
 namespace nsort {
 namespace seg {
@@ -157,20 +158,7 @@ __global__ void seg_owner_kernel(Params p) {
 
 // ---- the persistent kernel ------------------------------------------------
 
-// Waits (thread 0 only) until *ctr >= target, for about two seconds at most;
-// on time-out records NSORT_ETIMEOUT and returns.
-__device__ void wait_at_least(unsigned long long *ctr, unsigned long long target, int *status) {
-  for (unsigned long long spins = 0;; ++spins) {
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(ctr) : "memory");
-    if (v >= target) return;
-    if (spins > (1ull << 24)) {
-      atomicCAS(status, (int)NSORT_OK, (int)NSORT_ETIMEOUT);
-      return;
-    }
-    __nanosleep(128);
-  }
-}
+
 
 // Marks one item of segment s finished: every thread fences its own
 // stores, then one thread bumps the counter.
@@ -358,7 +346,8 @@ __device__ void merge_tile(const Params &p, void *smem, int64_t *split_sh, int64
   const int64_t L = p.off[sid + 1] - off;
   const int64_t T = (L + p.tile - 1) / p.tile;
   const int P = ceil_log2(T);
-  if (tid == 0) wait_at_least(&p.done[sid], (unsigned long long)level * T, &p.ctrl->status);
+  if (tid == 0)
+    wait_at_least(&p.done[sid], (unsigned long long)level * T, &p.ctrl->status, 2000000000ull);
   __syncthreads();
   const bool src_tmp = ((P - level + 1) & 1) != 0;
   const bool dst_tmp = ((P - level) & 1) != 0;
@@ -385,7 +374,17 @@ __device__ void merge_tile(const Params &p, void *smem, int64_t *split_sh, int64
     if (lane == 0) split_sh[1] = r;
   }
   __syncthreads();
-  const int64_t a_beg = split_sh[0], a_end = split_sh[1];
+  int64_t a_beg = split_sh[0], a_end = split_sh[1];
+  {
+    // keep both slices inside their runs and summing to the tile, whatever the
+    // splitters say (they are exact for sorted runs)
+    const int64_t d0 = out0 - pair0, d1 = out1 - pair0;
+    const int64_t lo0 = d0 - lb > 0 ? d0 - lb : 0, hi0 = d0 < la ? d0 : la;
+    a_beg = a_beg < lo0 ? lo0 : (a_beg > hi0 ? hi0 : a_beg);
+    const int64_t lo1 = d1 - lb > a_beg ? d1 - lb : a_beg;
+    const int64_t hi1 = a_beg + (d1 - d0) < la ? a_beg + (d1 - d0) : la;
+    a_end = a_end < lo1 ? lo1 : (a_end > hi1 ? hi1 : a_end);
+  }
   const int na = (int)(a_end - a_beg);
   const int count = (int)(out1 - out0);
   const int nb = count - na;

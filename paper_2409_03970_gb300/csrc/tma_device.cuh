@@ -48,14 +48,15 @@ __device__ __forceinline__ uint64_t global_ns() {
 }
 
 // Waits for the phase with the given parity to complete; gives up after
-// about two seconds (measured on the global timer, whatever each try_wait
-// blocks for) and returns false.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// limit_ns (default about two seconds, measured on the global timer,
+// whatever each try_wait blocks for) and returns false.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
+                                          uint64_t limit_ns = 2000000000ull) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   for (;;) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (global_ns() - t0 > 2000000000ull) return false;
+    if (global_ns() - t0 > limit_ns) return false;
   }
 }
 
@@ -95,6 +96,26 @@ __device__ __forceinline__ void bulk_wait_all() {
 // that memory by the bulk-copy engine.
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Waits (one thread) until *ctr >= target, for limit_ns at most (on the
+// global timer); on time-out records NSORT_ETIMEOUT (5) in *status and
+// returns false.
+__device__ __forceinline__ bool wait_at_least(unsigned long long *ctr, unsigned long long target,
+                                              int *status, uint64_t limit_ns) {
+  uint64_t t0 = 0;
+  for (unsigned long long spins = 0;; ++spins) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(ctr) : "memory");
+    if (v >= target) return true;
+    if (spins == 0) {
+      t0 = global_ns();
+    } else if (!(spins & 63) && global_ns() - t0 > limit_ns) {
+      atomicCAS(status, 0, 5);
+      return false;
+    }
+    __nanosleep(128);
+  }
 }
 
 // Store that asks L2 to keep the line (evict-last priority): for the small

@@ -104,6 +104,8 @@ def _load():
         lib.nsort_policy_pick_batch.restype = i32
         lib.nsort_policy_arena_replay.argtypes = [u64, i64p, i32, i64p]
         lib.nsort_policy_arena_replay.restype = i32
+        lib.nsort_selftest_wait.argtypes = [vp, sz, ctypes.c_uint32, vp]
+        lib.nsort_selftest_wait.restype = i32
         lib.nsort_keys_noalloc.argtypes = [vp, vp, u64, i32, vp]
         lib.nsort_keys_noalloc.restype = i32
         lib.nsort_trace_enable.argtypes = [i32]
@@ -280,6 +282,12 @@ class SortServer:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def nsort_selftest_wait(tmp, limit_us: int = 20000, stream=None) -> int:
+    """Runs the library's bounded waits on events that never happen (test hook)."""
+    return _load().nsort_selftest_wait(_ptr(tmp), tmp.numel() if hasattr(tmp, "numel") else 512,
+                                       limit_us, _stream(stream))
 
 
 def policy_pick_batch(queue, batch_max_keys, max_batch=4096, max_batch_keys=1 << 24):
