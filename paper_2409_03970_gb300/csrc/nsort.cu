@@ -146,7 +146,7 @@ template <int NT, int DT, bool FINAL>
 __global__ void __launch_bounds__(NT) tile_sort_pairs_kernel(const uint32_t *kin,
                                                              const uint32_t *vin,
                                                              uint32_t *kout, uint32_t *vout,
-                                                             int64_t n) {
+                                                             int64_t n, uint32_t *samp) {
   constexpr int TILE = NT * 16;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   uint64_t *s = reinterpret_cast<uint64_t *>(smem_raw);
@@ -180,6 +180,8 @@ __global__ void __launch_bounds__(NT) tile_sort_pairs_kernel(const uint32_t *kin
   const bool full = count == TILE && aligned16(kout + base) && aligned16(vout + base);
   store_run<16, FINAL ? DT : DT_U32>(ko, kout + base, count, full);
   store_run<16, DT_U32>(vo, vout + base, count, full);
+  if (!FINAL && samp && !(tid & (SAMPLE / 16 - 1)) && tid * 16 < count)
+    store_keep_in_l2(samp + (base + tid * 16) / SAMPLE, ko[0]);
 }
 
 // Clamps a tile's A co-ranks so that both slices stay inside their runs and
@@ -435,14 +437,17 @@ __device__ __forceinline__ SmemSlices smem_slices(const PairTile &g) {
   return l;
 }
 
-// Issues the bulk copies of tile g into buf (lane 0 of warp 0, into a
-// buffer no thread is reading).  Each slice's window is rounded out to
-// 16-byte boundaries, so up to 3 elements past a slice land in its sentinel
-// area (the warps overwrite them with sentinels before merging); windows
-// are clipped at n_al = n & ~3, past which the warps load the at most 3
+// Issues the bulk copies of tile g into buf (and, for pairs, of the values
+// into vbuf at the same offsets); lane 0 of warp 0, into buffers no thread
+// is reading.  Each slice's window is rounded out to 16-byte boundaries, so
+// up to 3 elements past a slice land in the gap behind it (overwritten by
+// sentinels, or never read by the bounds-checked merge); windows are
+// clipped at n_al = n & ~3, past which the warps load the at most 3
 // remaining elements themselves.
-__device__ __forceinline__ void issue_tile(const uint32_t *__restrict__ src, int64_t n_al,
-                                           const PairTile &g, uint32_t *buf, uint64_t *bar) {
+__device__ __forceinline__ void issue_tile(const uint32_t *__restrict__ src,
+                                           const uint32_t *__restrict__ vsrc, int64_t n_al,
+                                           const PairTile &g, uint32_t *buf, uint32_t *vbuf,
+                                           uint64_t *bar) {
   const SmemSlices l = smem_slices(g);
   const int64_t aw0 = g.a_off & ~int64_t(3);
   int64_t aw1 = (g.a_off + g.na + 3) & ~int64_t(3);
@@ -452,36 +457,48 @@ __device__ __forceinline__ void issue_tile(const uint32_t *__restrict__ src, int
   bw1 = bw1 < n_al ? bw1 : n_al;
   const uint32_t bytes_a = (g.na > 0 && aw1 > aw0) ? (uint32_t)((aw1 - aw0) * 4) : 0u;
   const uint32_t bytes_b = (g.nb > 0 && bw1 > bw0) ? (uint32_t)((bw1 - bw0) * 4) : 0u;
-  mbar_arrive_expect_tx(bar, bytes_a + bytes_b);
+  mbar_arrive_expect_tx(bar, (bytes_a + bytes_b) * (vsrc ? 2u : 1u));
   if (bytes_a) bulk_load(buf, src + aw0, bytes_a, bar);
   if (bytes_b) bulk_load(buf + l.base_b, src + bw0, bytes_b, bar);
+  if (vsrc) {
+    if (bytes_a) bulk_load(vbuf, vsrc + aw0, bytes_a, bar);
+    if (bytes_b) bulk_load(vbuf + l.base_b, vsrc + bw0, bytes_b, bar);
+  }
 }
 
-// Per tile, one CTA-wide barrier: after it, every thread is done with the
-// previous tile, so lane 0 of warp 0 can reuse that buffer for the next
-// tile's copies while the CTA merges this one.  Every warp writes the
-// sentinels (and, at the array's end, the last elements) it will read
-// itself, so no other barrier is needed; each warp's outputs are contiguous
-// (32 * VT keys), so each warp stages and bulk-stores its own part with
-// warp-level synchronisation only.  Lane 0 of warp 0 loads the splitters of
-// the tile after next one iteration early, off the critical path.
-template <int NT, int VT, int DT_OUT>
-__global__ void __launch_bounds__(NT, 4) merge_keys_tma_kernel(
-    const uint32_t *__restrict__ src, uint32_t *__restrict__ dst, int64_t n, int64_t run,
+// Persistent merge pass with bulk copies, keys (PAIRS = false) or stable
+// key/value pairs (PAIRS = true).  Per tile, one CTA-wide barrier: after it,
+// every thread is done with the previous tile, so lane 0 of warp 0 can reuse
+// that buffer for the next tile's copies while the CTA merges this one.
+// Keys: every warp writes the largest-key sentinels it will read itself and
+// merges without bounds checks (equal keys are equal bits).  Pairs: the
+// merge keeps its bounds checks (a real largest key must win over a
+// sentinel to stay stable), records where each output came from and
+// gathers the values from shared memory.  Each warp's outputs are
+// contiguous (32 * VT), so each warp stages and bulk-stores its own part
+// with warp-level synchronisation only.  Lane 0 of warp 0 loads the
+// splitters of the tile after next one iteration early.
+template <int NT, int VT, int DT_OUT, bool PAIRS>
+__global__ void __launch_bounds__(NT, PAIRS ? 3 : 4) merge_tma_kernel(
+    const uint32_t *__restrict__ src, const uint32_t *__restrict__ vsrc,
+    uint32_t *__restrict__ dst, uint32_t *__restrict__ vdst, int64_t n, int64_t run,
     int64_t tpp, int64_t num_tiles, const int64_t *__restrict__ split, int *status,
     uint32_t *samp, int reverse) {
   constexpr int TILE = NT * VT;
   constexpr int WOUT = 32 * VT;                       // outputs per warp
-  // A window + sentinels, B window + sentinels, rounding slack
+  // A window + gap, B window + gap, rounding slack
   constexpr int IN_LEN = (TILE + 2 * SENT + 16) & ~3;
-  static_assert(SENT >= VT + 1, "each run needs VT sentinels past its end");
+  static_assert(SENT >= (PAIRS ? VT + 2 : VT + 1), "the gap behind each run covers a merge's overrun");
   static_assert(SENT == 32, "one sentinel per lane and slice");
   static_assert(WOUT % 4 == 0, "warp output slices must be 16-byte multiples");
   static_assert(WOUT <= 32 * SAMPLE, "one sample per lane and warp slice");
-  // dynamic shared memory: [in_buf 0][in_buf 1][out_buf] (TMA_MERGE_SMEM)
+  // dynamic shared memory: keys [in 0][in 1] | values [in 0][in 1] | keys out | values out
   extern __shared__ __align__(128) unsigned char tma_smem[];
   uint32_t(*in_buf)[IN_LEN] = reinterpret_cast<uint32_t(*)[IN_LEN]>(tma_smem);
-  uint32_t *out_buf = reinterpret_cast<uint32_t *>(tma_smem) + 2 * IN_LEN;
+  uint32_t(*vin_buf)[IN_LEN] =
+      reinterpret_cast<uint32_t(*)[IN_LEN]>(tma_smem + (PAIRS ? 2 * IN_LEN * 4 : 0));
+  uint32_t *out_buf = reinterpret_cast<uint32_t *>(tma_smem) + (PAIRS ? 4 : 2) * IN_LEN;
+  uint32_t *vout_buf = out_buf + TILE;
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ PairTile desc[2];   // geometry of the tile in each buffer, written by thread 0
   const int tid = threadIdx.x;
@@ -503,7 +520,7 @@ __global__ void __launch_bounds__(NT, 4) merge_keys_tma_kernel(
       const int64_t u = tile_of(t);
       desc[0] = pair_tile_from(u, n, run, tpp, TILE, split[u],
                                u + 1 < num_tiles ? split[u + 1] : 0);
-      issue_tile(src, n_al, desc[0], in_buf[0], &bar[0]);
+      issue_tile(src, PAIRS ? vsrc : nullptr, n_al, desc[0], in_buf[0], vin_buf[0], &bar[0]);
     }
     if (t + G < num_tiles) {
       const int64_t u = tile_of(t + G);
@@ -514,6 +531,7 @@ __global__ void __launch_bounds__(NT, 4) merge_keys_tma_kernel(
   __syncthreads();
   bool ok = true;
   uint32_t *wout = out_buf + warp * WOUT;
+  uint32_t *wvout = vout_buf + warp * WOUT;
   for (int it = 0; t < num_tiles; ++it, t += G) {
     const int b = it & 1;
     const int64_t tn = t + G;
@@ -529,7 +547,8 @@ __global__ void __launch_bounds__(NT, 4) merge_keys_tma_kernel(
     // every thread is past the previous tile: its buffer and descriptor are free
     if (tid == 0 && tn < num_tiles) {
       desc[b ^ 1] = pair_tile_from(tile_of(tn), n, run, tpp, TILE, pf0, pf1);
-      issue_tile(src, n_al, desc[b ^ 1], in_buf[b ^ 1], &bar[b ^ 1]);
+      issue_tile(src, PAIRS ? vsrc : nullptr, n_al, desc[b ^ 1], in_buf[b ^ 1], vin_buf[b ^ 1],
+                 &bar[b ^ 1]);
       const int64_t tp = tn + G;
       if (tp < num_tiles) {
         const int64_t u = tile_of(tp);
@@ -540,41 +559,65 @@ __global__ void __launch_bounds__(NT, 4) merge_keys_tma_kernel(
     const PairTile g = desc[b];
     const SmemSlices l = smem_slices(g);
     uint32_t *s = in_buf[b];
+    uint32_t *sv = vin_buf[b];
     const int a0 = l.sh_a, b0 = l.base_b + l.sh_b;
-    // this warp's own sentinels and array-end elements (same values in every warp)
+    // this warp's own array-end elements (and sentinels, for keys); the same
+    // values in every warp
     if (g.a_off + g.na > n_al || g.b_off + g.nb > n_al) {
       if (lane < 3) {
         const int64_t i = (g.a_off > n_al ? g.a_off : n_al) + lane;
-        if (i < g.a_off + g.na) s[a0 + (int)(i - g.a_off)] = __ldg(src + i);
+        if (i < g.a_off + g.na) {
+          s[a0 + (int)(i - g.a_off)] = __ldg(src + i);
+          if (PAIRS) sv[a0 + (int)(i - g.a_off)] = __ldg(vsrc + i);
+        }
       } else if (lane < 6) {
         const int64_t i = (g.b_off > n_al ? g.b_off : n_al) + (lane - 3);
-        if (i < g.b_off + g.nb) s[b0 + (int)(i - g.b_off)] = __ldg(src + i);
+        if (i < g.b_off + g.nb) {
+          s[b0 + (int)(i - g.b_off)] = __ldg(src + i);
+          if (PAIRS) sv[b0 + (int)(i - g.b_off)] = __ldg(vsrc + i);
+        }
       }
     }
-    s[a0 + g.na + lane] = 0xFFFFFFFFu;
-    s[b0 + g.nb + lane] = 0xFFFFFFFFu;
+    if (!PAIRS) {
+      s[a0 + g.na + lane] = 0xFFFFFFFFu;
+      s[b0 + g.nb + lane] = 0xFFFFFFFFu;
+    }
     fence_proxy_async_smem();   // ordered before later bulk copies into this buffer
     __syncwarp();
     const int diag = tid * VT < g.count ? tid * VT : g.count;
     const int ai = merge_path_plain(s, a0, g.na, b0, g.nb, diag);
     uint32_t o[VT];
-    serial_merge_sentinel<VT>(s, a0 + ai, b0 + diag - ai, o);
-    // this warp's slice of the output: stage, then one bulk store by lane 0
+    int from[VT];
+    if (PAIRS) serial_merge_plain<VT, true>(s, a0 + ai, a0 + g.na, b0 + diag - ai, b0 + g.nb, o, from);
+    else serial_merge_sentinel<VT>(s, a0 + ai, b0 + diag - ai, o);
+    uint32_t ov[VT];
+    if (PAIRS) {
+#pragma unroll
+      for (int k = 0; k < VT; ++k) ov[k] = sv[from[k]];
+    }
+    // this warp's slice of the output: stage, then one bulk store per array
     const int w0 = warp * WOUT;
     const int wcount = g.count - w0 < WOUT ? g.count - w0 : WOUT;
-    if (lane == 0) bulk_wait_read_all();   // the warp's previous store has left wout
+    if (lane == 0) bulk_wait_read_all();   // the warp's previous stores have left its slices
     __syncwarp();
     if (g.count == TILE) {
 #pragma unroll
-      for (int k = 0; k < VT; ++k) wout[lane * VT + k] = from_key(o[k], DT_OUT);
+      for (int k = 0; k < VT; ++k) {
+        wout[lane * VT + k] = from_key(o[k], DT_OUT);
+        if (PAIRS) wvout[lane * VT + k] = ov[k];
+      }
     } else {
 #pragma unroll
-      for (int k = 0; k < VT; ++k)
-        if (tid * VT + k < g.count) wout[lane * VT + k] = from_key(o[k], DT_OUT);
+      for (int k = 0; k < VT; ++k) {
+        if (tid * VT + k < g.count) {
+          wout[lane * VT + k] = from_key(o[k], DT_OUT);
+          if (PAIRS) wvout[lane * VT + k] = ov[k];
+        }
+      }
     }
     fence_proxy_async_smem();
     __syncwarp();
-    if (samp && wcount > 0) {   // every SAMPLE-th output of the pass, for the next partition
+    if (samp && wcount > 0) {   // every SAMPLE-th output key, for the next partition
       const int64_t gb = g.out0 + w0;
       const int e = (int)((SAMPLE - (gb & (SAMPLE - 1))) & (SAMPLE - 1)) + SAMPLE * lane;
       if (e < wcount) store_keep_in_l2(samp + (gb + e) / SAMPLE, wout[e]);
@@ -583,9 +626,13 @@ __global__ void __launch_bounds__(NT, 4) merge_keys_tma_kernel(
       const int body = wcount & ~3;
       if (lane == 0 && body) {
         bulk_store(dst + g.out0 + w0, wout, (uint32_t)body * 4u);
+        if (PAIRS) bulk_store(vdst + g.out0 + w0, wvout, (uint32_t)body * 4u);
         bulk_commit();
       }
-      if (lane < (wcount & 3)) dst[g.out0 + w0 + body + lane] = wout[body + lane];
+      if (lane < (wcount & 3)) {
+        dst[g.out0 + w0 + body + lane] = wout[body + lane];
+        if (PAIRS) vdst[g.out0 + w0 + body + lane] = wvout[body + lane];
+      }
     }
   }
   if (lane == 0) bulk_wait_all();
@@ -607,10 +654,17 @@ constexpr int TMA_MERGE_NT = 128;   // persistent merge pass: 128 threads x 31 =
 constexpr int TMA_MERGE_VT = 31;
 constexpr int TMA_MERGE_TILE = TMA_MERGE_NT * TMA_MERGE_VT;
 
-// dynamic shared memory of merge_keys_tma_kernel: two input buffers and the
-// output staging area (IN_LEN words each input; TILE words out)
-constexpr size_t TMA_MERGE_SMEM =
-    sizeof(uint32_t) * (2 * ((TMA_MERGE_TILE + 2 * 32 + 16) & ~3) + TMA_MERGE_TILE);
+constexpr int TMA_PMERGE_NT = 128;  // pairs: 128 threads x 15 = 1920 outputs
+constexpr int TMA_PMERGE_VT = 15;
+constexpr int TMA_PMERGE_TILE = TMA_PMERGE_NT * TMA_PMERGE_VT;
+
+// dynamic shared memory of merge_tma_kernel: input buffers (two per array)
+// and output staging (one per array)
+constexpr size_t tma_merge_smem(int tile, bool pairs) {
+  return sizeof(uint32_t) * ((pairs ? 4 : 2) * ((tile + 2 * 32 + 16) & ~3) + (pairs ? 2 : 1) * tile);
+}
+constexpr size_t TMA_MERGE_SMEM = tma_merge_smem(TMA_MERGE_TILE, false);
+constexpr size_t TMA_PMERGE_SMEM = tma_merge_smem(TMA_PMERGE_TILE, true);
 
 constexpr int KEYS_SORT_TILE = KEYS_SORT_NT * 16;
 constexpr size_t KEYS_SORT_SMEM = sizeof(uint32_t) * merge_smem_len<uint32_t>(KEYS_SORT_TILE, 16);
@@ -637,8 +691,8 @@ Plan make_plan(int kind, uint64_t n) {
   const bool pairs = kind == NSORT_KIND_PAIRS;
   p.n = (int64_t)n;
   p.sort_tile = pairs ? PAIRS_SORT_TILE : KEYS_SORT_TILE;
-  // keys: the bulk-copy pass's tile; the staged-load fallback uses MERGE_TILE
-  p.merge_tile = pairs ? PMERGE_TILE : TMA_MERGE_TILE;
+  // the bulk-copy pass's tile; the staged-load fallback uses (P)MERGE_TILE
+  p.merge_tile = pairs ? TMA_PMERGE_TILE : TMA_MERGE_TILE;
   const int64_t runs = (p.n + p.sort_tile - 1) / p.sort_tile;
   p.merge_passes = 0;
   while ((int64_t(1) << p.merge_passes) < runs) ++p.merge_passes;
@@ -646,11 +700,10 @@ Plan make_plan(int kind, uint64_t n) {
   // splitters: enough for the power-of-two tiling and for the pair-aligned
   // tiling of every pass
   int64_t max_tiles = p.num_merge_tiles;
-  if (!pairs) {
-    for (int pass = 0; pass < p.merge_passes; ++pass) {
-      const int64_t t = pair_tiles(p.n, (int64_t)p.sort_tile << pass, TMA_MERGE_TILE, nullptr);
-      if (t > max_tiles) max_tiles = t;
-    }
+  for (int pass = 0; pass < p.merge_passes; ++pass) {
+    const int64_t t = pair_tiles(p.n, (int64_t)p.sort_tile << pass,
+                                 pairs ? TMA_PMERGE_TILE : TMA_MERGE_TILE, nullptr);
+    if (t > max_tiles) max_tiles = t;
   }
   const size_t kb = align_up((size_t)n * 4, 256);
   p.status_off = 0;
@@ -658,9 +711,7 @@ Plan make_plan(int kind, uint64_t n) {
   p.vals_off = p.keys_off + kb;
   p.split_off = pairs ? p.vals_off + kb : p.keys_off + kb;
   p.samp_off = p.split_off + align_up((size_t)(max_tiles + 1) * sizeof(int64_t), 256);
-  p.total = p.merge_passes == 0
-                ? 0
-                : p.samp_off + (pairs ? 0 : align_up((size_t)(n / SAMPLE + 2) * 4, 256));
+  p.total = p.merge_passes == 0 ? 0 : p.samp_off + align_up((size_t)(n / SAMPLE + 2) * 4, 256);
   return p;
 }
 
@@ -738,10 +789,10 @@ static int ensure_pairs_smem_attr() {
 
 static void launch_tile_sort_pairs(const uint32_t *kin, const uint32_t *vin, uint32_t *kout,
                                    uint32_t *vout, int64_t n, int dt, bool final_pass,
-                                   unsigned grid, cudaStream_t st) {
+                                   unsigned grid, uint32_t *samp, cudaStream_t st) {
 #define NSORT_TSP(DT, FIN)                                                      \
   tile_sort_pairs_kernel<PAIRS_SORT_NT, DT, FIN><<<grid, PAIRS_SORT_NT, PAIRS_SORT_SMEM, st>>>( \
-      kin, vin, kout, vout, n)
+      kin, vin, kout, vout, n, samp)
   if (dt == DT_U32) { if (final_pass) NSORT_TSP(DT_U32, true); else NSORT_TSP(DT_U32, false); }
   else if (dt == DT_I32) { if (final_pass) NSORT_TSP(DT_I32, true); else NSORT_TSP(DT_I32, false); }
   else { if (final_pass) NSORT_TSP(DT_F32, true); else NSORT_TSP(DT_F32, false); }
@@ -765,54 +816,74 @@ static void launch_partition(const uint32_t *src, int64_t n, int64_t run, const 
   partition_kernel<<<blocks, 256, 0, st>>>(src, n, run, tile, p.num_merge_tiles, split);
 }
 
-// Persistent merge pass: SMs x resident CTAs, found once per device.
-static int tma_merge_grid(int64_t tiles) {
-  static std::atomic<int> cached[64];
+template <int NT, int VT, bool PAIRS>
+static void tma_merge_attrs(size_t smem) {
+  const void *fns[3] = {(const void *)merge_tma_kernel<NT, VT, DT_U32, PAIRS>,
+                        (const void *)merge_tma_kernel<NT, VT, DT_I32, PAIRS>,
+                        (const void *)merge_tma_kernel<NT, VT, DT_F32, PAIRS>};
+  for (const void *f : fns) {   // opt in to the dynamic shared memory; prefer it over L1
+    cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  }
+}
+
+// Persistent merge pass: SMs x resident CTAs, found once per device and kind.
+static int tma_merge_grid(int64_t tiles, bool pairs) {
+  static std::atomic<int> cached[2][64];
   int dev = 0;
   cudaGetDevice(&dev);
-  int g = dev < 64 ? cached[dev].load() : 0;
+  int g = dev < 64 ? cached[pairs][dev].load() : 0;
   if (g == 0) {
     int sms = 0, occ = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // opt in to the dynamic shared memory, and prefer shared memory over L1
-    const void *fns[3] = {(const void *)merge_keys_tma_kernel<TMA_MERGE_NT, TMA_MERGE_VT, DT_U32>,
-                          (const void *)merge_keys_tma_kernel<TMA_MERGE_NT, TMA_MERGE_VT, DT_I32>,
-                          (const void *)merge_keys_tma_kernel<TMA_MERGE_NT, TMA_MERGE_VT, DT_F32>};
-    for (const void *f : fns) {
-      cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TMA_MERGE_SMEM);
-      cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (pairs) {
+      tma_merge_attrs<TMA_PMERGE_NT, TMA_PMERGE_VT, true>(TMA_PMERGE_SMEM);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &occ, merge_tma_kernel<TMA_PMERGE_NT, TMA_PMERGE_VT, DT_U32, true>, TMA_PMERGE_NT,
+          TMA_PMERGE_SMEM);
+    } else {
+      tma_merge_attrs<TMA_MERGE_NT, TMA_MERGE_VT, false>(TMA_MERGE_SMEM);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &occ, merge_tma_kernel<TMA_MERGE_NT, TMA_MERGE_VT, DT_U32, false>, TMA_MERGE_NT,
+          TMA_MERGE_SMEM);
     }
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &occ, merge_keys_tma_kernel<TMA_MERGE_NT, TMA_MERGE_VT, DT_U32>, TMA_MERGE_NT,
-        TMA_MERGE_SMEM);
     g = (sms > 0 ? sms : 1) * (occ > 0 ? occ : 1);
-    if (dev < 64) cached[dev].store(g);
+    if (dev < 64) cached[pairs][dev].store(g);
   }
   return (int)(tiles < g ? tiles : g);
 }
 
+// One bulk-copy merge pass (keys when vsrc is null, else stable pairs).
 // samp_in: samples of src (from the previous stage); samp_out: where this
 // pass writes the samples of dst (nullptr for the last pass).
-static void launch_merge_keys_tma(const uint32_t *src, uint32_t *dst, int64_t n, int64_t run,
-                                  int64_t *split, int *status, int dt_out, const uint32_t *samp_in,
-                                  uint32_t *samp_out, int reverse, cudaStream_t st) {
+static void launch_merge_tma(const uint32_t *src, const uint32_t *vsrc, uint32_t *dst,
+                             uint32_t *vdst, int64_t n, int64_t run, int64_t *split, int *status,
+                             int dt_out, const uint32_t *samp_in, uint32_t *samp_out, int reverse,
+                             cudaStream_t st) {
+  const bool pairs = vsrc != nullptr;
+  const int tile = pairs ? TMA_PMERGE_TILE : TMA_MERGE_TILE;
   int64_t tpp = 0;
-  const int64_t tiles = pair_tiles(n, run, TMA_MERGE_TILE, &tpp);
+  const int64_t tiles = pair_tiles(n, run, tile, &tpp);
   {
     TraceScope tr(TK_PARTITION, st);
     partition_sampled_kernel<<<(unsigned)((tiles + 255) / 256), 256, 0, st>>>(
-        src, samp_in, n, run, tpp, TMA_MERGE_TILE, tiles, split);
+        src, samp_in, n, run, tpp, tile, tiles, split);
   }
-  const unsigned grid = (unsigned)tma_merge_grid(tiles);
-  TraceScope tr(TK_MERGE_KEYS, st);
-#define NSORT_MKT(DT)                                                                   \
-  merge_keys_tma_kernel<TMA_MERGE_NT, TMA_MERGE_VT, DT>                                   \
-      <<<grid, TMA_MERGE_NT, TMA_MERGE_SMEM, st>>>(src, dst, n, run, tpp, tiles, split, status, \
-                                                   samp_out, reverse)
-  if (dt_out == DT_U32) NSORT_MKT(DT_U32);
-  else if (dt_out == DT_I32) NSORT_MKT(DT_I32);
-  else NSORT_MKT(DT_F32);
-#undef NSORT_MKT
+  const unsigned grid = (unsigned)tma_merge_grid(tiles, pairs);
+  TraceScope tr(pairs ? TK_MERGE_PAIRS : TK_MERGE_KEYS, st);
+#define NSORT_MT(NT, VT, DT, P, SMEM)                                                      \
+  merge_tma_kernel<NT, VT, DT, P><<<grid, NT, SMEM, st>>>(src, vsrc, dst, vdst, n, run, tpp, \
+                                                        tiles, split, status, samp_out, reverse)
+  if (!pairs) {
+    if (dt_out == DT_U32) NSORT_MT(TMA_MERGE_NT, TMA_MERGE_VT, DT_U32, false, TMA_MERGE_SMEM);
+    else if (dt_out == DT_I32) NSORT_MT(TMA_MERGE_NT, TMA_MERGE_VT, DT_I32, false, TMA_MERGE_SMEM);
+    else NSORT_MT(TMA_MERGE_NT, TMA_MERGE_VT, DT_F32, false, TMA_MERGE_SMEM);
+  } else {
+    if (dt_out == DT_U32) NSORT_MT(TMA_PMERGE_NT, TMA_PMERGE_VT, DT_U32, true, TMA_PMERGE_SMEM);
+    else if (dt_out == DT_I32) NSORT_MT(TMA_PMERGE_NT, TMA_PMERGE_VT, DT_I32, true, TMA_PMERGE_SMEM);
+    else NSORT_MT(TMA_PMERGE_NT, TMA_PMERGE_VT, DT_F32, true, TMA_PMERGE_SMEM);
+  }
+#undef NSORT_MT
 }
 
 // ---- the sorts ------------------------------------------------------------
@@ -845,8 +916,8 @@ int sort_keys_impl(const uint32_t *in, uint32_t *out, int64_t n, int dt, void *t
       // the partition reads the samples of this pass's input before the
       // merge overwrites them with the samples of its output
       // the tile sort writes low to high; passes then alternate direction
-      launch_merge_keys_tma(bufs[cur], bufs[cur ^ 1], n, run, split, status, dt_out, samp,
-                            pass == p.merge_passes - 1 ? nullptr : samp, (pass & 1) == 0, st);
+      launch_merge_tma(bufs[cur], nullptr, bufs[cur ^ 1], nullptr, n, run, split, status, dt_out,
+                       samp, pass == p.merge_passes - 1 ? nullptr : samp, (pass & 1) == 0, st);
     } else {
       {
         TraceScope tr(TK_PARTITION, st);
@@ -868,29 +939,37 @@ int sort_pairs_impl(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, ui
   if (rc != NSORT_OK) return rc;
   const Plan p = make_plan(NSORT_KIND_PAIRS, (uint64_t)n);
   char *t = static_cast<char *>(tmp);
-  uint32_t *kb[2] = {kout, reinterpret_cast<uint32_t *>(t + p.keys_off)};
-  uint32_t *vb[2] = {vout, reinterpret_cast<uint32_t *>(t + p.vals_off)};
+  uint32_t *kb[2] = {kout, p.merge_passes ? reinterpret_cast<uint32_t *>(t + p.keys_off) : nullptr};
+  uint32_t *vb[2] = {vout, p.merge_passes ? reinterpret_cast<uint32_t *>(t + p.vals_off) : nullptr};
   int64_t *split = p.merge_passes ? reinterpret_cast<int64_t *>(t + p.split_off) : nullptr;
-  if (p.merge_passes && cudaMemsetAsync(t + p.status_off, 0, sizeof(int), st) != cudaSuccess)
+  int *status = p.merge_passes ? reinterpret_cast<int *>(t + p.status_off) : nullptr;
+  uint32_t *samp = p.merge_passes ? reinterpret_cast<uint32_t *>(t + p.samp_off) : nullptr;
+  if (status && cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess)
     return launch_status("cudaMemsetAsync");
+  // the bulk-copy merge pass needs 16-byte aligned ping-pong buffers
+  const bool tma = !((reinterpret_cast<uintptr_t>(kout) | reinterpret_cast<uintptr_t>(vout)) & 15);
   int cur = p.merge_passes % 2;
   const int64_t tiles = (n + p.sort_tile - 1) / p.sort_tile;
   {
     TraceScope tr(TK_TILE_SORT_PAIRS, st);
     launch_tile_sort_pairs(kin, vin, kb[cur], vb[cur], n, dt, p.merge_passes == 0,
-                           (unsigned)tiles, st);
+                           (unsigned)tiles, tma ? samp : nullptr, st);
   }
   rc = launch_status("tile_sort_pairs");
   for (int pass = 0; rc == NSORT_OK && pass < p.merge_passes; ++pass) {
     const int64_t run = (int64_t)p.sort_tile << pass;
-    {
-      TraceScope tr(TK_PARTITION, st);
-      launch_partition(kb[cur], n, run, p, PMERGE_TILE, split, st);
-    }
-    {
+    const int dt_out = pass == p.merge_passes - 1 ? dt : DT_U32;
+    if (tma) {
+      launch_merge_tma(kb[cur], vb[cur], kb[cur ^ 1], vb[cur ^ 1], n, run, split, status, dt_out,
+                       samp, pass == p.merge_passes - 1 ? nullptr : samp, (pass & 1) == 0, st);
+    } else {
+      {
+        TraceScope tr(TK_PARTITION, st);
+        launch_partition(kb[cur], n, run, p, PMERGE_TILE, split, st);
+      }
       TraceScope tr(TK_MERGE_PAIRS, st);
-      launch_merge_pairs(kb[cur], vb[cur], kb[cur ^ 1], vb[cur ^ 1], n, run, split,
-                         pass == p.merge_passes - 1 ? dt : DT_U32, (unsigned)p.num_merge_tiles, st);
+      launch_merge_pairs(kb[cur], vb[cur], kb[cur ^ 1], vb[cur ^ 1], n, run, split, dt_out,
+                         (unsigned)p.num_merge_tiles, st);
     }
     rc = launch_status("merge_pairs");
     cur ^= 1;

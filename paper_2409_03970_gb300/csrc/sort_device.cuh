@@ -255,17 +255,20 @@ __device__ __forceinline__ int merge_path_plain(const uint32_t *s, int a0, int n
 }
 
 // Serial merge on unpadded shared memory (indices into s): VT outputs of the
-// stable merge of s[a, a_end) and s[b, b_end).  Reads at most VT + 1
-// elements past the larger end.
-template <int VT>
+// stable merge of s[a, a_end) and s[b, b_end) (A first on ties).  Reads at
+// most VT + 1 elements past the larger end.  With TRACK, src[k] receives
+// the index in s that output k came from.
+template <int VT, bool TRACK = false>
 __device__ __forceinline__ void serial_merge_plain(const uint32_t *s, int a, int a_end, int b,
-                                                   int b_end, uint32_t (&out)[VT]) {
+                                                   int b_end, uint32_t (&out)[VT],
+                                                   int (&src)[VT]) {
   uint32_t ka = s[a];
   uint32_t kb = s[b];
 #pragma unroll
   for (int k = 0; k < VT; ++k) {
     const bool take_a = (b >= b_end) || (a < a_end && ka <= kb);
     out[k] = take_a ? ka : kb;
+    if (TRACK) src[k] = take_a ? a : b;
     const int nx = (take_a ? a : b) + 1;
     const uint32_t kn = s[nx];
     a = take_a ? nx : a;
