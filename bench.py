@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched (segmented) and served measurements")
-    ap.add_argument("--workload", choices=["plain", "segmented", "served"], default="plain",
+    ap.add_argument("--workload", choices=["plain", "segmented", "served", "ablation"],
+                    default="plain",
                     help="plain: the headline line (with batched/served extras); segmented / "
                          "served: that measurement alone, as its own line")
     ap.add_argument("--served-duration", type=float, default=10.0,
@@ -359,6 +360,50 @@ def bench_configs(nsort, torch):
 
 # ---- batched (segmented) and served measurements -----------------------------
 
+def bench_ablation(nsort, torch):
+    """Column-network and keys-per-thread ablation (Table 1 / Table 2).
+
+    in_register: GKeys/s of producing sorted runs of X keys (column sort
+    with IPT keys per thread, then log2(X / IPT) warp merge levels) on 2^23
+    u32 keys that stay in L2 between repetitions (64 MiB in + out), as the
+    paper times its in-register sort on cache-resident data.  block_sort:
+    GKeys/s of the whole block sort (tiles of 512 * IPT keys) on 2^26 keys
+    (256 MiB, larger than L2), the production tile sort being best / 16."""
+    from paper_2409_03970_gb300 import inputs
+    fams = {"best": nsort.NET_BEST, "oddeven": nsort.NET_ODDEVEN, "bitonic": nsort.NET_BITONIC}
+    ipts = (4, 8, 16, 32)
+    out = {"comparators": {f: {w: len(nsort.nsort_network(c, w)) for w in ipts}
+                           for f, c in fams.items()}}
+
+    def table(n, runs_of, reps):
+        x = torch.from_numpy(inputs.keys(n, "u32", "uniform", seed=21).view(np.int32)).cuda()
+        y = torch.empty_like(x)
+        res = {}
+        for f, c in fams.items():
+            res[f] = {}
+            for ipt in ipts:
+                res[f][ipt] = {}
+                for run in runs_of(ipt):
+                    def fn(run=run, ipt=ipt, c=c):
+                        rc = nsort.nsort_runs(x, y, n, c, ipt, run)
+                        if rc != nsort.OK:
+                            raise nsort.NsortError(rc, "nsort_runs")
+                    ms = time_sort(nsort, torch, fn, reps=reps, warm=3)
+                    res[f][ipt][run] = n / (ms / 1e3) / 1e9
+        del x, y
+        return res
+
+    n_reg = 1 << 23
+    out["in_register"] = {"n": n_reg, "unit": "GKeys/s", "l2": "resident (64 MiB in + out)",
+                          "table": table(n_reg, lambda ipt: [ipt << l for l in range(6)], 21)}
+    n_blk = 1 << 26
+    blk = table(n_blk, lambda ipt: [512 * ipt], 11)
+    out["block_sort"] = {"n": n_blk, "unit": "GKeys/s", "l2": "inputs (256 MiB) larger than L2",
+                         "table": {f: {ipt: v[512 * ipt] for ipt, v in t.items()}
+                                   for f, t in blk.items()}}
+    return out
+
+
 def bench_batched(nsort, torch, nseg: int, reps: int = 5):
     """100,000 uint32 arrays (lengths log-uniform in [1, 65536], uniform keys)
     sorted by one graph-captured nsort_segmented launch with the autotuned
@@ -565,6 +610,12 @@ def main():
                         "value": r["batched_gkeys_s"], "unit": "GKeys/s", "n_gpus": 1,
                         "higher_is_better": True, "data": "synthetic", "dtype": "u32",
                         "config": r, "vs_baseline": None}
+            elif args.workload == "ablation":
+                r = bench_ablation(nsort, torch)
+                line = {"metric": "block-sort GKeys/s by column network and keys per thread",
+                        "value": r["block_sort"]["table"]["best"][16], "unit": "GKeys/s",
+                        "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+                        "dtype": "u32", "config": r, "vs_baseline": None}
             else:
                 r = bench_served(nsort, torch, args.served_duration)
                 line = {"metric": "served sort stream: keys/s and p50/p99 latency vs plain FIFO",

@@ -104,6 +104,24 @@ def odd_even_sorter(n: int):
     return rec(list(range(n)))
 
 
+def best32():
+    """The fewest-comparator 32-input network Table 1 bounds from above
+    (n = 32, "135~185"): Green's network on each half, then Batcher's
+    odd-even merge of the two sorted halves, 2 * 60 + 65 = 185
+    comparators."""
+    upper = [(lo + 16, hi + 16) for lo, hi in green16()]
+    return green16() + upper + _odd_even_merge(list(range(32)))
+
+
+def best_sorter(n: int):
+    """Table 1's "Asymmetric Network" column for n = 4, 8, 16, 32: the
+    odd-even networks for 4 and 8 (5 and 19 comparators, the fewest
+    possible), Green's network for 16, best32() for 32."""
+    if n in (4, 8):
+        return odd_even_sorter(n)
+    return {16: green16, 32: best32}[n]()
+
+
 # --- analysis -----------------------------------------------------------
 
 def depth(net) -> int:
@@ -141,6 +159,19 @@ def zero_one_failures_sorter(net, n: int) -> int:
     for w in range(n - 1):
         bad |= wires[w] & ~wires[w + 1]
     return int(bad.sum())
+
+
+def split_halves(net, n: int):
+    """Splits a network on n wires into the longest prefix whose comparators
+    each stay inside one half and the rest: (lower-half prefix, upper-half
+    prefix shifted to wires [0, n/2), suffix)."""
+    h = n // 2
+    k = 0
+    while k < len(net) and (net[k][1] < h or net[k][0] >= h):
+        k += 1
+    lower = [c for c in net[:k] if c[1] < h]
+    upper = [(lo - h, hi - h) for lo, hi in net[:k] if lo >= h]
+    return lower, upper, net[k:]
 
 
 def zero_one_failures_merger(net, m: int) -> int:

@@ -1,0 +1,239 @@
+// Network and keys-per-thread ablation of the block sort (C ABI in
+// include/nsort_ablation.h): Table 1's networks (bitonic, odd-even, best)
+// as the column sort, with 4, 8, 16 or 32 keys per thread (Table 2's R).
+// The kernels reuse the production column sort, warp merge and block merge
+// code (sort_device.cuh), so only the network and the width change.
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "nsort.h"
+#include "nsort_ablation.h"
+#include "nsort_internal.h"
+#include "sort_device.cuh"
+
+namespace nsort {
+namespace {
+
+constexpr int ABL_NT = 512;   // threads per CTA, as in the production tile sort
+
+template <int FAMILY>
+struct NetColumns {
+  template <typename K, int W>
+  __device__ __forceinline__ static void sort(K (&r)[W]) { column_sort_net<FAMILY, W>(r); }
+};
+
+__device__ __forceinline__ bool is_aligned16(const void *p) {
+  return !(reinterpret_cast<uintptr_t>(p) & 15);
+}
+
+// Thread-contiguous load of keys [e0, e0 + W); keys past n read as the
+// largest key, which sorts behind every real key and is never stored.
+template <int W>
+__device__ __forceinline__ void load_contig(const uint32_t *in, int64_t n, int64_t e0,
+                                            uint32_t (&r)[W]) {
+  if (e0 + W <= n && is_aligned16(in + e0)) {
+#pragma unroll
+    for (int q = 0; q < W / 4; ++q) {
+      const uint4 v = reinterpret_cast<const uint4 *>(in + e0)[q];
+      r[4 * q + 0] = v.x;
+      r[4 * q + 1] = v.y;
+      r[4 * q + 2] = v.z;
+      r[4 * q + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < W; ++k) r[k] = e0 + k < n ? in[e0 + k] : 0xFFFFFFFFu;
+  }
+}
+
+template <int W>
+__device__ __forceinline__ void store_contig(uint32_t *out, int64_t n, int64_t e0,
+                                             const uint32_t (&r)[W]) {
+  if (e0 + W <= n && is_aligned16(out + e0)) {
+#pragma unroll
+    for (int q = 0; q < W / 4; ++q)
+      reinterpret_cast<uint4 *>(out + e0)[q] =
+          make_uint4(r[4 * q + 0], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < W; ++k)
+      if (e0 + k < n) out[e0 + k] = r[k];
+  }
+}
+
+// One thread per group of W keys: the column sort alone.
+template <int FAMILY, int W>
+__global__ void __launch_bounds__(256) network_kernel(const uint32_t *in, uint32_t *out,
+                                                      int64_t groups) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= groups) return;
+  uint32_t r[W];
+#pragma unroll
+  for (int k = 0; k < W; ++k) r[k] = in[g * W + k];
+  column_sort_net<FAMILY, W>(r);
+#pragma unroll
+  for (int k = 0; k < W; ++k) out[g * W + k] = r[k];
+}
+
+// The in-register sort: thread t of the grid sorts keys [IPT t, IPT t + IPT)
+// with the network, then `levels` levels of the warp's flip merger make
+// sorted runs of IPT * 2^levels.  Every lane takes part in the shuffles,
+// including lanes wholly past n (they hold only padding).
+template <int FAMILY, int IPT>
+__global__ void __launch_bounds__(ABL_NT) warp_runs_kernel(const uint32_t *in, uint32_t *out,
+                                                           int64_t n, int levels) {
+  const int64_t e0 = ((int64_t)blockIdx.x * ABL_NT + threadIdx.x) * IPT;
+  uint32_t r[IPT];
+  load_contig<IPT>(in, n, e0, r);
+  column_sort_net<FAMILY, IPT>(r);
+  warp_merge<IPT>(r, threadIdx.x & 31, levels);
+  store_contig<IPT>(out, n, e0, r);
+}
+
+// The block sort of one tile of ABL_NT * IPT keys, as the production tile
+// sort does it (coalesced 16-byte loads in any assignment, the column sort,
+// the warp merge, the shared-memory merges), with the network of FAMILY.
+template <int FAMILY, int IPT>
+__global__ void __launch_bounds__(ABL_NT) block_runs_kernel(const uint32_t *in, uint32_t *out,
+                                                            int64_t n) {
+  constexpr int TILE = ABL_NT * IPT;
+  extern __shared__ __align__(16) unsigned char abl_smem[];   // merge_smem_len(TILE, IPT) words
+  uint32_t *s = reinterpret_cast<uint32_t *>(abl_smem);
+  const int tid = threadIdx.x;
+  const int64_t base = (int64_t)blockIdx.x * TILE;
+  const int count = (int)(n - base < TILE ? n - base : TILE);
+  uint32_t r[IPT];
+  if (count == TILE && is_aligned16(in + base)) {
+    const uint4 *p = reinterpret_cast<const uint4 *>(in + base);
+#pragma unroll
+    for (int q = 0; q < IPT / 4; ++q) {
+      const uint4 v = p[tid + ABL_NT * q];
+      r[4 * q + 0] = v.x;
+      r[4 * q + 1] = v.y;
+      r[4 * q + 2] = v.z;
+      r[4 * q + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < IPT / 4; ++q) {
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        const int e = 4 * (tid + ABL_NT * q) + w;
+        r[4 * q + w] = e < count ? in[base + e] : 0xFFFFFFFFu;
+      }
+    }
+  }
+  sort_tile_in_block<ABL_NT, IPT, NetColumns<FAMILY>>(r, s);
+  store_contig<IPT>(out + base, count, (int64_t)tid * IPT, r);
+}
+
+template <int IPT>
+constexpr size_t block_smem_bytes() {
+  return sizeof(uint32_t) * (size_t)merge_smem_len<uint32_t>(ABL_NT * IPT, IPT);
+}
+
+int launch_error(const char *what) {
+  const cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) return NSORT_OK;
+  set_last_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return NSORT_ECUDA;
+}
+
+template <int FAMILY, int W>
+int apply_w(const uint32_t *in, uint32_t *out, int64_t groups, cudaStream_t st) {
+  const unsigned grid = (unsigned)((groups + 255) / 256);
+  network_kernel<FAMILY, W><<<grid, 256, 0, st>>>(in, out, groups);
+  return launch_error("nsort_network_apply");
+}
+
+template <int FAMILY>
+int apply_f(const uint32_t *in, uint32_t *out, int64_t groups, int w, cudaStream_t st) {
+  switch (w) {
+    case 4: return apply_w<FAMILY, 4>(in, out, groups, st);
+    case 8: return apply_w<FAMILY, 8>(in, out, groups, st);
+    case 16: return apply_w<FAMILY, 16>(in, out, groups, st);
+    default: return apply_w<FAMILY, 32>(in, out, groups, st);
+  }
+}
+
+template <int FAMILY, int IPT>
+int runs_fi(const uint32_t *in, uint32_t *out, int64_t n, int levels, bool block,
+            cudaStream_t st) {
+  const int64_t tile = (int64_t)ABL_NT * IPT;
+  const unsigned grid = (unsigned)((n + tile - 1) / tile);
+  if (block) {
+    constexpr size_t smem = block_smem_bytes<IPT>();
+    if (cudaFuncSetAttribute(block_runs_kernel<FAMILY, IPT>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return launch_error("cudaFuncSetAttribute");
+    block_runs_kernel<FAMILY, IPT><<<grid, ABL_NT, smem, st>>>(in, out, n);
+  } else {
+    warp_runs_kernel<FAMILY, IPT><<<grid, ABL_NT, 0, st>>>(in, out, n, levels);
+  }
+  return launch_error("nsort_runs");
+}
+
+template <int FAMILY>
+int runs_f(const uint32_t *in, uint32_t *out, int64_t n, int ipt, int levels, bool block,
+           cudaStream_t st) {
+  switch (ipt) {
+    case 4: return runs_fi<FAMILY, 4>(in, out, n, levels, block, st);
+    case 8: return runs_fi<FAMILY, 8>(in, out, n, levels, block, st);
+    case 16: return runs_fi<FAMILY, 16>(in, out, n, levels, block, st);
+    default: return runs_fi<FAMILY, 32>(in, out, n, levels, block, st);
+  }
+}
+
+bool valid_width(int w) { return w == 4 || w == 8 || w == 16 || w == 32; }
+bool valid_family(int f) { return f == NET_BITONIC || f == NET_ODDEVEN || f == NET_BEST; }
+
+}  // namespace
+}  // namespace nsort
+
+using namespace nsort;
+
+extern "C" int nsort_network(int family, int width, int32_t *lo, int32_t *hi, int cap) {
+  if (!valid_family(family) || !valid_width(width)) return -1;
+  const CmpList l = make_network(family, width);
+  for (int c = 0; c < l.n && c < cap; ++c) {
+    if (lo) lo[c] = l.lo[c];
+    if (hi) hi[c] = l.hi[c];
+  }
+  return l.n;
+}
+
+extern "C" int nsort_network_apply(const uint32_t *d_in, uint32_t *d_out, uint64_t groups,
+                                   int family, int width, void *stream) {
+  if (!valid_family(family) || !valid_width(width) || groups > (uint64_t(1) << 32))
+    return NSORT_EINVAL;
+  if (groups == 0) return NSORT_OK;
+  if (!d_in || !d_out) return NSORT_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t g = (int64_t)groups;
+  switch (family) {
+    case NET_BITONIC: return apply_f<NET_BITONIC>(d_in, d_out, g, width, st);
+    case NET_ODDEVEN: return apply_f<NET_ODDEVEN>(d_in, d_out, g, width, st);
+    default: return apply_f<NET_BEST>(d_in, d_out, g, width, st);
+  }
+}
+
+extern "C" int nsort_runs(const uint32_t *d_in, uint32_t *d_out, uint64_t n, int family, int ipt,
+                          uint64_t run, void *stream) {
+  if (!valid_family(family) || !valid_width(ipt) || n > MAX_KEYS) return NSORT_EINVAL;
+  int levels = -1;
+  for (int l = 0; l <= 5; ++l)
+    if (run == (uint64_t)ipt << l) levels = l;
+  const bool block = run == (uint64_t)ABL_NT * ipt;
+  if (levels < 0 && !block) return NSORT_EINVAL;
+  if (n == 0) return NSORT_OK;
+  if (!d_in || !d_out) return NSORT_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t nn = (int64_t)n;
+  switch (family) {
+    case NET_BITONIC: return runs_f<NET_BITONIC>(d_in, d_out, nn, ipt, levels, block, st);
+    case NET_ODDEVEN: return runs_f<NET_ODDEVEN>(d_in, d_out, nn, ipt, levels, block, st);
+    default: return runs_f<NET_BEST>(d_in, d_out, nn, ipt, levels, block, st);
+  }
+}

@@ -30,36 +30,6 @@ namespace nsort {
 
 // ---------------------------------------------------------------- kernels
 
-// Sorts one tile of NT*16 elements that is already in registers (16 per
-// thread, any assignment).  On return thread t holds tile elements
-// [16t, 16t + 16) of the sorted tile in r.  s is scratch (merge_smem_len).
-template <int NT, typename K>
-__device__ __forceinline__ void sort_tile_in_block(K (&r)[16], K *s) {
-  constexpr int TILE = NT * 16;
-  const int tid = threadIdx.x;
-  const int lane = tid & 31;
-  column_sort16(r);
-  warp_merge512(r, lane);
-  if (TILE == 512) return;
-  const int e0 = tid * 16;
-#pragma unroll
-  for (int k = 0; k < 16; ++k) s[pidx<K>(e0 + k)] = r[k];
-  int unused[16];
-#pragma unroll 1
-  for (int run = 512; run < TILE; run <<= 1) {
-    __syncthreads();
-    const int g0 = e0 & ~(2 * run - 1);
-    const int diag = e0 - g0;
-    const int ai = merge_path_smem(s, g0, run, g0 + run, run, diag);
-    serial_merge<16, false>(s, g0 + ai, g0 + run, g0 + run + diag - ai, g0 + 2 * run, r, unused);
-    if (2 * run < TILE) {
-      __syncthreads();
-#pragma unroll
-      for (int k = 0; k < 16; ++k) s[pidx<K>(e0 + k)] = r[k];
-    }
-  }
-}
-
 // Thread t stores its VT consecutive outputs o[] at out[t*VT ...], mapped
 // back to bit patterns by DT_OUT.  Full, 16-byte aligned tiles use 128-bit
 // stores straight from registers; others store element by element.
@@ -131,7 +101,7 @@ __global__ void __launch_bounds__(NT) tile_sort_keys_kernel(const uint32_t *in, 
       }
     }
   }
-  sort_tile_in_block<NT>(r, s);
+  sort_tile_in_block<NT, 16, Green16Columns>(r, s);
   store_run<16, FINAL ? DT : DT_U32>(r, out + base, count, full);
   static_assert(SAMPLE % 16 == 0, "a sample starts a thread's run of 16");
   if (!FINAL && samp && !(tid & (SAMPLE / 16 - 1)) && tid * 16 < count)
@@ -169,7 +139,7 @@ __global__ void __launch_bounds__(NT) tile_sort_pairs_kernel(const uint32_t *kin
                                : ~0ull;
     }
   }
-  sort_tile_in_block<NT>(r, s);
+  sort_tile_in_block<NT, 16, Green16Columns>(r, s);
   // every thread passed a barrier after the values were staged
   uint32_t ko[16], vo[16];
 #pragma unroll

@@ -21,6 +21,8 @@
 
 #include <cstdint>
 
+#include "networks_device.cuh"
+
 namespace nsort {
 
 enum { DT_U32 = 0, DT_I32 = 1, DT_F32 = 2 };
@@ -74,25 +76,23 @@ __device__ __forceinline__ void ce(K &a, K &b) {
   a = lo;
 }
 
-// ---- column sort: the 16-input network (Sec. 2.3, Table 1) --------------
-// M. W. Green's network, 60 comparators in 10 layers: four layers compare
-// the wires whose indices differ in one bit (a 4-cube), six more finish.
+// ---- column sort (Sec. 2.3, Table 1) -------------------------------------
+// Runs the network of the given family and width (networks_device.cuh) on
+// the thread's W registers.  The comparator list is a compile-time constant
+// and the loop is fully unrolled, so every index is a constant.
+template <int FAMILY, int W, typename K>
+__device__ __forceinline__ void column_sort_net(K (&r)[W]) {
+  constexpr CmpList net = make_network(FAMILY, W);
+  static_assert(net.n > 0, "no network of this family and width");
+#pragma unroll
+  for (int c = 0; c < net.n; ++c) ce(r[net.lo[c]], r[net.hi[c]]);
+}
+
+// The production column sort: M. W. Green's 60-comparator, depth-10
+// network (the "best" 16-input network of Table 1).
 template <typename K>
 __device__ __forceinline__ void column_sort16(K (&r)[16]) {
-#pragma unroll
-  for (int bit = 1; bit < 16; bit <<= 1) {
-#pragma unroll
-    for (int i = 0; i < 16; ++i)
-      if (!(i & bit)) ce(r[i], r[i | bit]);
-  }
-  ce(r[5], r[10]); ce(r[6], r[9]); ce(r[3], r[12]); ce(r[13], r[14]);
-  ce(r[7], r[11]); ce(r[1], r[2]); ce(r[4], r[8]);
-  ce(r[1], r[4]); ce(r[7], r[13]); ce(r[2], r[8]); ce(r[11], r[14]);
-  ce(r[5], r[6]); ce(r[9], r[10]);
-  ce(r[2], r[4]); ce(r[11], r[13]); ce(r[3], r[8]); ce(r[7], r[12]);
-  ce(r[6], r[8]); ce(r[10], r[12]); ce(r[3], r[5]); ce(r[7], r[9]);
-  ce(r[3], r[4]); ce(r[5], r[6]); ce(r[7], r[8]); ce(r[9], r[10]); ce(r[11], r[12]);
-  ce(r[6], r[7]); ce(r[8], r[9]);
+  column_sort_net<NET_BEST, 16>(r);
 }
 
 // ---- warp-level flip merging network (Sec. 2.4) -------------------------
@@ -109,17 +109,11 @@ __device__ __forceinline__ K keep(bool lower, K mine, K other) {
   return lower ? kmin(mine, other) : kmax(mine, other);
 }
 
-// 8-input network for 8 keys per thread: Batcher's odd-even merge sort,
-// 19 comparators in 6 layers, which is also the fewest possible for n = 8
-// (Table 1, n = 8).
+// 8 keys per thread: Batcher's odd-even merge sort, 19 comparators in 6
+// layers, which is also the fewest possible for n = 8 (Table 1, n = 8).
 template <typename K>
 __device__ __forceinline__ void column_sort8(K (&r)[8]) {
-  ce(r[0], r[1]); ce(r[2], r[3]); ce(r[4], r[5]); ce(r[6], r[7]);
-  ce(r[0], r[2]); ce(r[1], r[3]); ce(r[4], r[6]); ce(r[5], r[7]);
-  ce(r[1], r[2]); ce(r[5], r[6]);
-  ce(r[0], r[4]); ce(r[1], r[5]); ce(r[2], r[6]); ce(r[3], r[7]);
-  ce(r[2], r[4]); ce(r[3], r[5]);
-  ce(r[1], r[2]); ce(r[3], r[4]); ce(r[5], r[6]);
+  column_sort_net<NET_ODDEVEN, 8>(r);
 }
 
 template <typename K>
@@ -145,11 +139,13 @@ __device__ __forceinline__ void thread_tail(K (&r)[IPT]) {
 // 2m-1-p of the 2m-element group: lane l ^ (2^j - 1), register IPT-1-k),
 // half-cleaner stages across lanes at lane distances 2^(j-2)..1, then the
 // in-thread tail.  In each cross-lane comparator the lower lane keeps the
-// minimum and the upper lane the maximum.
+// minimum and the upper lane the maximum.  With levels < 5 only the first
+// levels levels run: the warp then holds sorted runs of IPT * 2^levels.
 template <int IPT, typename K>
-__device__ __forceinline__ void warp_merge(K (&r)[IPT], int lane) {
+__device__ __forceinline__ void warp_merge(K (&r)[IPT], int lane, int levels = 5) {
 #pragma unroll
   for (int j = 1; j <= 5; ++j) {
+    if (j > levels) break;
     const int span = 1 << j;
     const bool lower = !(lane & (span >> 1));
 #pragma unroll
@@ -169,10 +165,6 @@ __device__ __forceinline__ void warp_merge(K (&r)[IPT], int lane) {
   }
 }
 
-template <typename K>
-__device__ __forceinline__ void warp_merge512(K (&r)[16], int lane) {
-  warp_merge<16>(r, lane);
-}
 
 // ---- merge path (Sec. 2.1: load-balanced partitioning) -------------------
 // Number of elements of A among the first `diag` outputs of the stable
@@ -324,6 +316,49 @@ __device__ __forceinline__ void serial_merge(const K *s, int a, int a_end, int b
     kb = take_a ? kb : kn;
     a += take_a;
     b += !take_a;
+  }
+}
+
+// ---- block sort (Sec. 2.1: in-register sort, then vectorized merges) -----
+// The 16-input column sort as a policy of the block sort; other policies
+// (other networks, other numbers of keys per thread) are plugged in by the
+// network ablation.
+struct Green16Columns {
+  template <typename K>
+  __device__ __forceinline__ static void sort(K (&r)[16]) { column_sort16(r); }
+};
+
+// Sorts one tile of NT*IPT elements that is already in registers (IPT per
+// thread, any assignment).  On return thread t holds tile elements
+// [IPT t, IPT t + IPT) of the sorted tile in r.  The thread's registers are
+// sorted by COLS, the warp merge makes runs of 32 IPT, and log2(NT/32)
+// shared-memory levels (a merge-path split per thread, then a serial merge
+// of IPT outputs) merge those pairwise.  s is scratch of
+// merge_smem_len<K>(NT * IPT, IPT) elements.
+template <int NT, int IPT, class COLS, typename K>
+__device__ __forceinline__ void sort_tile_in_block(K (&r)[IPT], K *s) {
+  constexpr int TILE = NT * IPT;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  COLS::sort(r);
+  warp_merge<IPT>(r, lane);
+  if (TILE == 32 * IPT) return;
+  const int e0 = tid * IPT;
+#pragma unroll
+  for (int k = 0; k < IPT; ++k) s[pidx<K>(e0 + k)] = r[k];
+  int unused[IPT];
+#pragma unroll 1
+  for (int run = 32 * IPT; run < TILE; run <<= 1) {
+    __syncthreads();
+    const int g0 = e0 & ~(2 * run - 1);
+    const int diag = e0 - g0;
+    const int ai = merge_path_smem(s, g0, run, g0 + run, run, diag);
+    serial_merge<IPT, false>(s, g0 + ai, g0 + run, g0 + run + diag - ai, g0 + 2 * run, r, unused);
+    if (2 * run < TILE) {
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < IPT; ++k) s[pidx<K>(e0 + k)] = r[k];
+    }
   }
 }
 

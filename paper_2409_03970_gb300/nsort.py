@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libnsort.so")
 U32, I32, F32 = 0, 1, 2
 KIND_KEYS, KIND_PAIRS, KIND_SEGMENTED, KIND_SEGMENTED_PAIRS = 0, 1, 2, 3
 OK, EINVAL, ENOMEM, ECUDA, EBUSY, ETIMEOUT, ENOTFOUND = range(7)
+NET_BITONIC, NET_ODDEVEN, NET_BEST = 0, 1, 2     # include/nsort_ablation.h
 
 _lock = threading.Lock()
 _lib = None
@@ -108,6 +109,13 @@ def _load():
         lib.nsort_selftest_wait.restype = i32
         lib.nsort_keys_noalloc.argtypes = [vp, vp, u64, i32, vp]
         lib.nsort_keys_noalloc.restype = i32
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        lib.nsort_network.argtypes = [i32, i32, i32p, i32p, i32]
+        lib.nsort_network.restype = i32
+        lib.nsort_network_apply.argtypes = [vp, vp, u64, i32, i32, vp]
+        lib.nsort_network_apply.restype = i32
+        lib.nsort_runs.argtypes = [vp, vp, u64, i32, i32, u64, vp]
+        lib.nsort_runs.restype = i32
         lib.nsort_trace_enable.argtypes = [i32]
         lib.nsort_trace_enable.restype = i32
         lib.nsort_trace_read.argtypes = [vp, i32, ip]
@@ -330,6 +338,31 @@ def nsort_keys_noalloc(keys_in, keys_out, n: int, dtype: int, stream=None) -> in
 class TraceEntry(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_char * 32), ("launches", ctypes.c_uint64),
                 ("total_ms", ctypes.c_double)]
+
+
+# ---- ablation of the column-sort network and keys per thread ------------
+
+def nsort_network(family: int, width: int):
+    """The comparator list (lo, hi) pairs the device column sort of this
+    family and width is generated from; None for an unknown one."""
+    n = _load().nsort_network(family, width, None, None, 0)
+    if n < 0:
+        return None
+    lo = (ctypes.c_int32 * max(n, 1))()
+    hi = (ctypes.c_int32 * max(n, 1))()
+    _load().nsort_network(family, width, lo, hi, n)
+    return [(lo[c], hi[c]) for c in range(n)]
+
+
+def nsort_network_apply(keys_in, keys_out, groups: int, family: int, width: int,
+                        stream=None) -> int:
+    return _load().nsort_network_apply(_ptr(keys_in), _ptr(keys_out), groups, family, width,
+                                       _stream(stream))
+
+
+def nsort_runs(keys_in, keys_out, n: int, family: int, ipt: int, run: int, stream=None) -> int:
+    return _load().nsort_runs(_ptr(keys_in), _ptr(keys_out), n, family, ipt, run,
+                              _stream(stream))
 
 
 def nsort_trace_enable(on: bool) -> int:

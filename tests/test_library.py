@@ -66,7 +66,7 @@ def test_temp_bytes(lib):
     assert 4 * n <= tb <= 4 * n + 8 * (n // mt + n // (2 * st) + 3) + 4 * (n // 64 + 2) + 1280
     tp = nsort.nsort_temp_bytes(nsort.KIND_PAIRS, n)
     _, pst, pmt = nsort.nsort_plan(nsort.KIND_PAIRS, n)
-    assert 8 * n <= tp <= 8 * n + 8 * (n // pmt + n // (2 * pst) + 3) + 1024
+    assert 8 * n <= tp <= 8 * n + 8 * (n // pmt + n // (2 * pst) + 3) + 4 * (n // 64 + 2) + 1280
     assert nsort.nsort_temp_bytes(99, n) == 0
 
 
@@ -85,3 +85,62 @@ def test_argument_validation_needs_no_gpu(lib):
     assert nsort.nsort_pairs(0x1000, 0x4000, 0x2000, 0x3000, big, nsort.F32, 0, 0, 0) == nsort.ENOMEM
     for s in range(7):
         assert lib.nsort_status_string(s)
+
+
+# ---- column-sort networks of the ablation (include/nsort_ablation.h) ----
+
+FAMILIES = {"bitonic": nsort.NET_BITONIC, "oddeven": nsort.NET_ODDEVEN, "best": nsort.NET_BEST}
+
+
+def test_library_networks_have_table1_sizes(lib, golden):
+    for n, bit, oe, amin, amax in golden("table1_comparators.txt"):
+        n = int(n)
+        assert len(nsort.nsort_network(nsort.NET_BITONIC, n)) == int(bit)
+        assert len(nsort.nsort_network(nsort.NET_ODDEVEN, n)) == int(oe)
+        assert int(amin) <= len(nsort.nsort_network(nsort.NET_BEST, n)) <= int(amax)
+    assert len(nsort.nsort_network(nsort.NET_BEST, 16)) == 60
+    assert len(nsort.nsort_network(nsort.NET_BEST, 32)) == 185
+
+
+@pytest.mark.parametrize("family", list(FAMILIES))
+def test_library_networks_sort_by_zero_one_principle(lib, family):
+    """The lists the device column sorts are generated from, checked on all
+    0-1 inputs (widths 4-16) and by composition (width 32)."""
+    from oracle import networks as N
+    f = FAMILIES[family]
+    for w in (4, 8, 16):
+        net = nsort.nsort_network(f, w)
+        assert all(0 <= lo < hi < w for lo, hi in net)
+        assert N.zero_one_failures_sorter(net, w) == 0
+    lower, upper, merge = N.split_halves(nsort.nsort_network(f, 32), 32)
+    assert N.zero_one_failures_sorter(lower, 16) == 0
+    assert N.zero_one_failures_sorter(upper, 16) == 0
+    assert N.zero_one_failures_merger(merge, 16) == 0
+
+
+def test_library_networks_are_the_named_networks(lib):
+    """Same comparators as the oracle's independently written generators;
+    the best 16-input network is Green's, comparator for comparator."""
+    from oracle import networks as N
+    for w in (4, 8, 16, 32):
+        assert set(nsort.nsort_network(nsort.NET_BITONIC, w)) == set(N.bitonic_sorter(w))
+        assert set(nsort.nsort_network(nsort.NET_ODDEVEN, w)) == set(N.odd_even_sorter(w))
+        assert set(nsort.nsort_network(nsort.NET_BEST, w)) == set(N.best_sorter(w))
+    assert nsort.nsort_network(nsort.NET_BEST, 16) == N.green16()
+    assert N.depth(nsort.nsort_network(nsort.NET_BEST, 16)) == 10
+
+
+def test_ablation_argument_validation_needs_no_gpu(lib):
+    assert nsort.nsort_network(3, 16) is None
+    assert nsort.nsort_network(nsort.NET_BEST, 12) is None
+    assert nsort.nsort_network_apply(0x1000, 0x1000, 4, nsort.NET_BEST, 12, 0) == nsort.EINVAL
+    assert nsort.nsort_network_apply(0x1000, 0x1000, 4, 7, 16, 0) == nsort.EINVAL
+    assert nsort.nsort_network_apply(0, 0, 0, nsort.NET_BEST, 16, 0) == nsort.OK
+    assert nsort.nsort_network_apply(0, 0x1000, 4, nsort.NET_BEST, 16, 0) == nsort.EINVAL
+    # run must be ipt * 2^L (L <= 5) or 512 * ipt
+    assert nsort.nsort_runs(0x1000, 0x1000, 100, nsort.NET_BEST, 16, 24, 0) == nsort.EINVAL
+    assert nsort.nsort_runs(0x1000, 0x1000, 100, nsort.NET_BEST, 16, 1024, 0) == nsort.EINVAL
+    assert nsort.nsort_runs(0x1000, 0x1000, 100, nsort.NET_BEST, 12, 12, 0) == nsort.EINVAL
+    assert nsort.nsort_runs(0x1000, 0x1000, 1 << 41, nsort.NET_BEST, 16, 16, 0) == nsort.EINVAL
+    assert nsort.nsort_runs(0, 0, 100, nsort.NET_BEST, 16, 16, 0) == nsort.EINVAL
+    assert nsort.nsort_runs(0, 0, 0, nsort.NET_BEST, 16, 8192, 0) == nsort.OK

@@ -60,3 +60,29 @@ def test_verifier_catches_a_dropped_comparator():
         assert N.zero_one_failures_sorter(broken, 16) > 0
     m = N.flip_merger(16)
     assert N.zero_one_failures_merger(m[1:], 16) > 0
+
+
+def test_best_sorters_within_table1(golden):
+    for n, _bit, _oe, amin, amax in golden("table1_comparators.txt"):
+        n = int(n)
+        assert int(amin) <= len(N.best_sorter(n)) <= int(amax)
+    assert len(N.best32()) == 185          # the upper bound of Table 1, n = 32
+
+
+@pytest.mark.parametrize("make", [lambda: N.bitonic_sorter(32), lambda: N.odd_even_sorter(32),
+                                  N.best32], ids=["bitonic", "oddeven", "best"])
+def test_32_input_sorters_by_composition(make):
+    """A network that first sorts each half and then merges any two sorted
+    halves sorts everything (0-1 principle, applied to the two phases):
+    each half's prefix is checked on all 2^16 0-1 inputs, the rest on all
+    17 x 17 pairs of sorted 0-1 halves."""
+    lower, upper, merge = N.split_halves(make(), 32)
+    assert N.zero_one_failures_sorter(lower, 16) == 0
+    assert N.zero_one_failures_sorter(upper, 16) == 0
+    assert N.zero_one_failures_merger(merge, 16) == 0
+
+
+def test_composition_check_catches_a_dropped_merge_comparator():
+    lower, upper, merge = N.split_halves(N.best32(), 32)
+    for drop in (0, 20, 64):
+        assert N.zero_one_failures_merger(merge[:drop] + merge[drop + 1:], 16) > 0
