@@ -361,14 +361,16 @@ def bench_configs(nsort, torch):
 # ---- batched (segmented) and served measurements -----------------------------
 
 def bench_ablation(nsort, torch):
-    """Column-network and keys-per-thread ablation (Table 1 / Table 2).
+    """Column-network, keys-per-thread and merger ablation (Tables 1-3).
 
     in_register: GKeys/s of producing sorted runs of X keys (column sort
     with IPT keys per thread, then log2(X / IPT) warp merge levels) on 2^23
     u32 keys that stay in L2 between repetitions (64 MiB in + out), as the
     paper times its in-register sort on cache-resident data.  block_sort:
     GKeys/s of the whole block sort (tiles of 512 * IPT keys) on 2^26 keys
-    (256 MiB, larger than L2), the production tile sort being best / 16."""
+    (256 MiB, larger than L2), the production tile sort being best / 16.
+    mergers: GKeys/s of merging sorted runs of L into 2L with the hybrid,
+    all-shuffle and serial merge-path mergers (Table 3), 2^23 keys in L2."""
     from paper_2409_03970_gb300 import inputs
     fams = {"best": nsort.NET_BEST, "oddeven": nsort.NET_ODDEVEN, "bitonic": nsort.NET_BITONIC}
     ipts = (4, 8, 16, 32)
@@ -396,6 +398,33 @@ def bench_ablation(nsort, torch):
     n_reg = 1 << 23
     out["in_register"] = {"n": n_reg, "unit": "GKeys/s", "l2": "resident (64 MiB in + out)",
                           "table": table(n_reg, lambda ipt: [ipt << l for l in range(6)], 21)}
+    # Table 3: merge two sorted runs of L into 2L, by merger and keys per thread
+    x = torch.from_numpy(inputs.keys(n_reg, "u32", "uniform", seed=22).view(np.int32)).cuda()
+    y = torch.empty_like(x)
+    mergers = {"hybrid": nsort.MERGE_HYBRID, "shuffle": nsort.MERGE_SHUFFLE,
+               "serial": nsort.MERGE_SERIAL}
+    mt = {}
+    for L in (8, 16, 32, 64, 128, 256):
+        rc = nsort.nsort_runs(x, x, n_reg, nsort.NET_BEST, 4, L) if L <= 128 else \
+            nsort.nsort_runs(x, x, n_reg, nsort.NET_BEST, 8, L)
+        if rc != nsort.OK:
+            raise nsort.NsortError(rc, "nsort_runs")
+        mt[f"2x{L}"] = {}
+        for m, code in mergers.items():
+            mt[f"2x{L}"][m] = {}
+            for ipt in ipts:
+                if L not in nsort.merge_run_lengths(code, ipt):
+                    continue
+
+                def fn(L=L, code=code, ipt=ipt):
+                    rc = nsort.nsort_merge_runs(x, y, n_reg, L, code, ipt)
+                    if rc != nsort.OK:
+                        raise nsort.NsortError(rc, "nsort_merge_runs")
+                ms = time_sort(nsort, torch, fn, reps=21, warm=3)
+                mt[f"2x{L}"][m][ipt] = n_reg / (ms / 1e3) / 1e9
+    del x, y
+    out["mergers"] = {"n": n_reg, "unit": "GKeys/s", "l2": "resident (64 MiB in + out)",
+                      "table": mt}
     n_blk = 1 << 26
     blk = table(n_blk, lambda ipt: [512 * ipt], 11)
     out["block_sort"] = {"n": n_blk, "unit": "GKeys/s", "l2": "inputs (256 MiB) larger than L2",

@@ -64,6 +64,32 @@ int nsort_network_apply(const uint32_t *d_in, uint32_t *d_out, uint64_t groups, 
 int nsort_runs(const uint32_t *d_in, uint32_t *d_out, uint64_t n, int family, int ipt,
                uint64_t run, void *stream);
 
+/* Mergers of Table 3 (Sec. 2.4). */
+typedef enum {
+    NSORT_MERGE_HYBRID = 0,   /* flip merger, lane-contiguous keys: shuffles while the compare
+                                 distance is >= ipt, then the in-thread tail (production) */
+    NSORT_MERGE_SHUFFLE = 1,  /* flip merger, lane-strided keys (key 32k + lane in register k):
+                                 every distance below 32 is a shuffle ("vectorized") */
+    NSORT_MERGE_SERIAL = 2    /* merge path in shared memory, then a serial merge of ipt
+                                 outputs per thread */
+} nsort_merger;
+
+/* Merges each pair of adjacent sorted runs of d_in, [2k run, (2k+1) run) and
+ * [(2k+1) run, (2k+2) run) (clipped to n), into the sorted run
+ * [2k run, (2k+2) run) of d_out, with `method` and `ipt` keys per thread
+ * (4, 8, 16, 32) in 512-thread CTAs.  run must be a power of two with
+ *   NSORT_MERGE_HYBRID    ipt <= run <= 16 ipt
+ *   NSORT_MERGE_SHUFFLE   1 <= run <= 16 ipt
+ *   NSORT_MERGE_SERIAL    ipt / 2 <= run <= 256 ipt
+ * else NSORT_EINVAL.  d_in must be sorted within each run of `run` keys;
+ * if it is not, d_out is unspecified (every access still stays inside the
+ * n keys of each buffer).  d_in and d_out hold n uint32 each (n up to
+ * 2^40) and may be equal.  Source: the
+ * hybrid and vectorized bitonic mergers of Sec. 2.4 (Table 3) and the
+ * merge-path serial merge of Sec. 2.1. */
+int nsort_merge_runs(const uint32_t *d_in, uint32_t *d_out, uint64_t n, uint64_t run,
+                     int method, int ipt, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -128,6 +128,142 @@ __global__ void __launch_bounds__(ABL_NT) block_runs_kernel(const uint32_t *in, 
   store_contig<IPT>(out + base, count, (int64_t)tid * IPT, r);
 }
 
+// ---- merger ablation (Sec. 2.4, Table 3) ----------------------------------
+// Three ways to merge every two adjacent sorted runs of L keys into one
+// sorted run of 2L, all with IPT keys per thread.
+
+// Hybrid (the production warp merge): lane l holds keys [IPT l, IPT l + IPT)
+// of its warp's chunk; one level of the flip merger with cross-lane stages
+// while the compare distance is at least IPT, then the in-thread tail.
+// Valid for IPT <= L <= 16 IPT.
+template <int IPT>
+__device__ __forceinline__ void hybrid_merge(uint32_t (&r)[IPT], int lane, int log2_span) {
+  switch (log2_span) {   // span = 2L / IPT lanes
+    case 1: warp_merge_level<1>(r, lane); break;
+    case 2: warp_merge_level<2>(r, lane); break;
+    case 3: warp_merge_level<3>(r, lane); break;
+    case 4: warp_merge_level<4>(r, lane); break;
+    default: warp_merge_level<5>(r, lane); break;
+  }
+}
+
+// All-shuffle ("vectorized") merge: lane l holds keys 32 k + l (k < IPT)
+// of its warp's chunk, so every compare distance below 32 is a shuffle and
+// only distances of 32 and more stay inside a thread.  The flip stage
+// compares key i with key i ^ (2L - 1); the half-cleaners compare key i
+// with key i ^ d for d = L/2 .. 1; the smaller index keeps the minimum.
+// Valid for 1 <= L <= 16 IPT.
+template <int LOG2L, int IPT>
+__device__ __forceinline__ void shuffle_merge_level(uint32_t (&r)[IPT], int lane) {
+  constexpr int L = 1 << LOG2L;
+  if constexpr (2 * L <= 32) {
+    const bool lower = !(lane & L);
+#pragma unroll
+    for (int k = 0; k < IPT; ++k) r[k] = keep(lower, r[k], shfl_x(r[k], 2 * L - 1));
+  } else {
+    // partner of (register k, lane l) is (k ^ KM, l ^ 31); k with bit L/32
+    // clear holds the smaller index
+    constexpr int KM = 2 * L / 32 - 1;
+#pragma unroll
+    for (int k = 0; k < IPT; ++k) {
+      if (k & (L / 32)) continue;
+      const int kp = k ^ KM;
+      const uint32_t for_k = shfl_x(r[kp], 31);
+      const uint32_t for_kp = shfl_x(r[k], 31);
+      r[k] = kmin(r[k], for_k);
+      r[kp] = kmax(r[kp], for_kp);
+    }
+  }
+#pragma unroll
+  for (int d = L / 2; d >= 1; d >>= 1) {
+    if (d >= 32) {
+#pragma unroll
+      for (int k = 0; k < IPT; ++k)
+        if (!(k & (d / 32))) ce(r[k], r[k + d / 32]);
+    } else {
+      const bool lo = !(lane & d);
+#pragma unroll
+      for (int k = 0; k < IPT; ++k) r[k] = keep(lo, r[k], shfl_x(r[k], d));
+    }
+  }
+}
+
+template <int IPT>
+__device__ __forceinline__ void shuffle_merge(uint32_t (&r)[IPT], int lane, int log2_l) {
+  switch (log2_l) {
+    case 0: shuffle_merge_level<0>(r, lane); break;
+    case 1: shuffle_merge_level<1>(r, lane); break;
+    case 2: shuffle_merge_level<2>(r, lane); break;
+    case 3: shuffle_merge_level<3>(r, lane); break;
+    case 4: shuffle_merge_level<4>(r, lane); break;
+    case 5: shuffle_merge_level<5>(r, lane); break;
+    case 6: if constexpr (IPT >= 4) shuffle_merge_level<6>(r, lane); break;
+    case 7: if constexpr (IPT >= 8) shuffle_merge_level<7>(r, lane); break;
+    case 8: if constexpr (IPT >= 16) shuffle_merge_level<8>(r, lane); break;
+    default: if constexpr (IPT >= 32) shuffle_merge_level<9>(r, lane); break;
+  }
+}
+
+enum { MERGE_HYBRID = 0, MERGE_SHUFFLE = 1, MERGE_SERIAL = 2 };
+
+template <int IPT>
+__global__ void __launch_bounds__(ABL_NT) hybrid_merge_kernel(const uint32_t *in, uint32_t *out,
+                                                              int64_t n, int log2_span) {
+  const int64_t e0 = ((int64_t)blockIdx.x * ABL_NT + threadIdx.x) * IPT;
+  uint32_t r[IPT];
+  load_contig<IPT>(in, n, e0, r);
+  hybrid_merge<IPT>(r, threadIdx.x & 31, log2_span);
+  store_contig<IPT>(out, n, e0, r);
+}
+
+template <int IPT>
+__global__ void __launch_bounds__(ABL_NT) shuffle_merge_kernel(const uint32_t *in, uint32_t *out,
+                                                               int64_t n, int log2_l) {
+  const int lane = threadIdx.x & 31;
+  const int64_t chunk = ((int64_t)blockIdx.x * ABL_NT + (threadIdx.x & ~31)) * IPT;
+  uint32_t r[IPT];
+#pragma unroll
+  for (int k = 0; k < IPT; ++k) {
+    const int64_t e = chunk + 32 * k + lane;
+    r[k] = e < n ? in[e] : 0xFFFFFFFFu;
+  }
+  shuffle_merge<IPT>(r, lane, log2_l);
+#pragma unroll
+  for (int k = 0; k < IPT; ++k) {
+    const int64_t e = chunk + 32 * k + lane;
+    if (e < n) out[e] = r[k];
+  }
+}
+
+// Serial merge path: the tile of ABL_NT * IPT keys is staged in shared
+// memory; thread t finds where its IPT outputs [IPT t, IPT t + IPT) start in
+// its pair of runs by a merge-path search and merges them serially.  Valid
+// for IPT / 2 <= L <= ABL_NT * IPT / 2.
+template <int IPT>
+__global__ void __launch_bounds__(ABL_NT) serial_merge_kernel(const uint32_t *in, uint32_t *out,
+                                                              int64_t n, int run) {
+  constexpr int TILE = ABL_NT * IPT;
+  extern __shared__ __align__(16) unsigned char abl_smem[];   // merge_smem_len(TILE, IPT) words
+  uint32_t *s = reinterpret_cast<uint32_t *>(abl_smem);
+  const int tid = threadIdx.x;
+  const int64_t base = (int64_t)blockIdx.x * TILE;
+  const int count = (int)(n - base < TILE ? n - base : TILE);
+#pragma unroll
+  for (int k = 0; k < IPT; ++k) {
+    const int e = tid + ABL_NT * k;
+    s[pidx<uint32_t>(e)] = e < count ? in[base + e] : 0xFFFFFFFFu;
+  }
+  __syncthreads();
+  const int e0 = tid * IPT;
+  const int g0 = e0 & ~(2 * run - 1);
+  const int diag = e0 - g0;
+  const int ai = merge_path_smem(s, g0, run, g0 + run, run, diag);
+  uint32_t r[IPT];
+  int unused[IPT];
+  serial_merge<IPT, false>(s, g0 + ai, g0 + run, g0 + run + diag - ai, g0 + 2 * run, r, unused);
+  store_contig<IPT>(out + base, count, (int64_t)e0, r);
+}
+
 template <int IPT>
 constexpr size_t block_smem_bytes() {
   return sizeof(uint32_t) * (size_t)merge_smem_len<uint32_t>(ABL_NT * IPT, IPT);
@@ -186,6 +322,28 @@ int runs_f(const uint32_t *in, uint32_t *out, int64_t n, int ipt, int levels, bo
   }
 }
 
+template <int IPT>
+int merge_i(const uint32_t *in, uint32_t *out, int64_t n, int method, int log2_l,
+            cudaStream_t st) {
+  const int64_t tile = (int64_t)ABL_NT * IPT;
+  const unsigned grid = (unsigned)((n + tile - 1) / tile);
+  if (method == MERGE_HYBRID) {
+    int log2_ipt = 0;
+    while ((1 << log2_ipt) < IPT) ++log2_ipt;
+    hybrid_merge_kernel<IPT><<<grid, ABL_NT, 0, st>>>(in, out, n, log2_l + 1 - log2_ipt);
+  } else if (method == MERGE_SHUFFLE) {
+    shuffle_merge_kernel<IPT><<<grid, ABL_NT, 0, st>>>(in, out, n, log2_l);
+  } else {
+    constexpr size_t smem = block_smem_bytes<IPT>();
+    if (cudaFuncSetAttribute(serial_merge_kernel<IPT>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return launch_error("cudaFuncSetAttribute");
+    serial_merge_kernel<IPT><<<grid, ABL_NT, smem, st>>>(in, out, n, 1 << log2_l);
+  }
+  return launch_error("nsort_merge_runs");
+}
+
 bool valid_width(int w) { return w == 4 || w == 8 || w == 16 || w == 32; }
 bool valid_family(int f) { return f == NET_BITONIC || f == NET_ODDEVEN || f == NET_BEST; }
 
@@ -235,5 +393,28 @@ extern "C" int nsort_runs(const uint32_t *d_in, uint32_t *d_out, uint64_t n, int
     case NET_BITONIC: return runs_f<NET_BITONIC>(d_in, d_out, nn, ipt, levels, block, st);
     case NET_ODDEVEN: return runs_f<NET_ODDEVEN>(d_in, d_out, nn, ipt, levels, block, st);
     default: return runs_f<NET_BEST>(d_in, d_out, nn, ipt, levels, block, st);
+  }
+}
+
+extern "C" int nsort_merge_runs(const uint32_t *d_in, uint32_t *d_out, uint64_t n, uint64_t run,
+                                int method, int ipt, void *stream) {
+  if (!valid_width(ipt) || n > MAX_KEYS || run == 0 || (run & (run - 1))) return NSORT_EINVAL;
+  const uint64_t u = (uint64_t)ipt;
+  bool ok = false;
+  if (method == MERGE_HYBRID) ok = run >= u && run <= 16 * u;
+  else if (method == MERGE_SHUFFLE) ok = run <= 16 * u;
+  else if (method == MERGE_SERIAL) ok = 2 * run >= u && run <= (uint64_t)ABL_NT * u / 2;
+  if (!ok) return NSORT_EINVAL;
+  if (n == 0) return NSORT_OK;
+  if (!d_in || !d_out) return NSORT_EINVAL;
+  int log2_l = 0;
+  while ((uint64_t(1) << log2_l) < run) ++log2_l;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t nn = (int64_t)n;
+  switch (ipt) {
+    case 4: return merge_i<4>(d_in, d_out, nn, method, log2_l, st);
+    case 8: return merge_i<8>(d_in, d_out, nn, method, log2_l, st);
+    case 16: return merge_i<16>(d_in, d_out, nn, method, log2_l, st);
+    default: return merge_i<32>(d_in, d_out, nn, method, log2_l, st);
   }
 }

@@ -133,38 +133,44 @@ __device__ __forceinline__ void thread_tail(K (&r)[IPT]) {
   }
 }
 
-// Lane l holds a sorted run of IPT in r[] (warp element IPT*l + k).  Merges
-// the 32 runs into one sorted run of 32*IPT in five levels.  Level j merges
-// groups of 2^(j-1) lanes pairwise: a flip stage (element p against element
-// 2m-1-p of the 2m-element group: lane l ^ (2^j - 1), register IPT-1-k),
-// half-cleaner stages across lanes at lane distances 2^(j-2)..1, then the
-// in-thread tail.  In each cross-lane comparator the lower lane keeps the
-// minimum and the upper lane the maximum.  With levels < 5 only the first
-// levels levels run: the warp then holds sorted runs of IPT * 2^levels.
-template <int IPT, typename K>
-__device__ __forceinline__ void warp_merge(K (&r)[IPT], int lane, int levels = 5) {
+// Lane l holds a sorted run of IPT in r[] (warp element IPT*l + k).  One
+// level J of the warp merge merges the sorted runs held by groups of
+// 2^(J-1) lanes pairwise: a flip stage (element p against element 2m-1-p of
+// the 2m-element group: lane l ^ (2^J - 1), register IPT-1-k), half-cleaner
+// stages across lanes at lane distances 2^(J-2)..1, then the in-thread
+// tail.  In each cross-lane comparator the lower lane keeps the minimum and
+// the upper lane the maximum.
+template <int J, int IPT, typename K>
+__device__ __forceinline__ void warp_merge_level(K (&r)[IPT], int lane) {
+  constexpr int span = 1 << J;
+  const bool lower = !(lane & (span >> 1));
 #pragma unroll
-  for (int j = 1; j <= 5; ++j) {
-    if (j > levels) break;
-    const int span = 1 << j;
-    const bool lower = !(lane & (span >> 1));
-#pragma unroll
-    for (int k = 0; k < IPT / 2; ++k) {
-      const K from_hi = shfl_x(r[IPT - 1 - k], span - 1);   // partner's mirror of r[k]
-      const K from_lo = shfl_x(r[k], span - 1);             // partner's mirror of r[IPT-1-k]
-      r[k] = keep(lower, r[k], from_hi);
-      r[IPT - 1 - k] = keep(lower, r[IPT - 1 - k], from_lo);
-    }
-#pragma unroll
-    for (int d = span >> 2; d >= 1; d >>= 1) {
-      const bool lo2 = !(lane & d);
-#pragma unroll
-      for (int k = 0; k < IPT; ++k) r[k] = keep(lo2, r[k], shfl_x(r[k], d));
-    }
-    thread_tail<IPT>(r);
+  for (int k = 0; k < IPT / 2; ++k) {
+    const K from_hi = shfl_x(r[IPT - 1 - k], span - 1);   // partner's mirror of r[k]
+    const K from_lo = shfl_x(r[k], span - 1);             // partner's mirror of r[IPT-1-k]
+    r[k] = keep(lower, r[k], from_hi);
+    r[IPT - 1 - k] = keep(lower, r[IPT - 1 - k], from_lo);
   }
+#pragma unroll
+  for (int d = span >> 2; d >= 1; d >>= 1) {
+    const bool lo2 = !(lane & d);
+#pragma unroll
+    for (int k = 0; k < IPT; ++k) r[k] = keep(lo2, r[k], shfl_x(r[k], d));
+  }
+  thread_tail<IPT>(r);
 }
 
+// The five levels merge the warp's 32 runs into one sorted run of 32*IPT.
+// With levels < 5 only the first levels levels run: the warp then holds
+// sorted runs of IPT * 2^levels.
+template <int IPT, typename K>
+__device__ __forceinline__ void warp_merge(K (&r)[IPT], int lane, int levels = 5) {
+  if (levels >= 1) warp_merge_level<1>(r, lane);
+  if (levels >= 2) warp_merge_level<2>(r, lane);
+  if (levels >= 3) warp_merge_level<3>(r, lane);
+  if (levels >= 4) warp_merge_level<4>(r, lane);
+  if (levels >= 5) warp_merge_level<5>(r, lane);
+}
 
 // ---- merge path (Sec. 2.1: load-balanced partitioning) -------------------
 // Number of elements of A among the first `diag` outputs of the stable

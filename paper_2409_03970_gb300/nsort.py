@@ -22,6 +22,7 @@ U32, I32, F32 = 0, 1, 2
 KIND_KEYS, KIND_PAIRS, KIND_SEGMENTED, KIND_SEGMENTED_PAIRS = 0, 1, 2, 3
 OK, EINVAL, ENOMEM, ECUDA, EBUSY, ETIMEOUT, ENOTFOUND = range(7)
 NET_BITONIC, NET_ODDEVEN, NET_BEST = 0, 1, 2     # include/nsort_ablation.h
+MERGE_HYBRID, MERGE_SHUFFLE, MERGE_SERIAL = 0, 1, 2
 
 _lock = threading.Lock()
 _lib = None
@@ -116,6 +117,8 @@ def _load():
         lib.nsort_network_apply.restype = i32
         lib.nsort_runs.argtypes = [vp, vp, u64, i32, i32, u64, vp]
         lib.nsort_runs.restype = i32
+        lib.nsort_merge_runs.argtypes = [vp, vp, u64, u64, i32, i32, vp]
+        lib.nsort_merge_runs.restype = i32
         lib.nsort_trace_enable.argtypes = [i32]
         lib.nsort_trace_enable.restype = i32
         lib.nsort_trace_read.argtypes = [vp, i32, ip]
@@ -363,6 +366,24 @@ def nsort_network_apply(keys_in, keys_out, groups: int, family: int, width: int,
 def nsort_runs(keys_in, keys_out, n: int, family: int, ipt: int, run: int, stream=None) -> int:
     return _load().nsort_runs(_ptr(keys_in), _ptr(keys_out), n, family, ipt, run,
                               _stream(stream))
+
+
+def nsort_merge_runs(keys_in, keys_out, n: int, run: int, method: int, ipt: int,
+                     stream=None) -> int:
+    return _load().nsort_merge_runs(_ptr(keys_in), _ptr(keys_out), n, run, method, ipt,
+                                    _stream(stream))
+
+
+def merge_run_lengths(method: int, ipt: int):
+    """The run lengths nsort_merge_runs accepts for this merger and width."""
+    lo, hi = {MERGE_HYBRID: (ipt, 16 * ipt), MERGE_SHUFFLE: (1, 16 * ipt),
+              MERGE_SERIAL: (max(1, ipt // 2), 256 * ipt)}[method]
+    out, r = [], 1
+    while r <= hi:
+        if r >= lo:
+            out.append(r)
+        r *= 2
+    return out
 
 
 def nsort_trace_enable(on: bool) -> int:

@@ -143,3 +143,43 @@ def test_block_sort_best16_equals_production_tile_sort(ns):
     out = torch.empty_like(x)
     assert ns.nsort_runs(x, out, n, ns.NET_BEST, 16, 8192, 0) == ns.OK
     np.testing.assert_array_equal(host(out), oracle_runs(bits, 8192))
+
+
+# ---- mergers of Table 3 (nsort_merge_runs) --------------------------------
+
+MERGERS = {"hybrid": 0, "shuffle": 1, "serial": 2}
+
+
+def merge_cases():
+    from paper_2409_03970_gb300 import nsort as N     # run-length rule only, no library call
+    for m, code in MERGERS.items():
+        for ipt in IPTS:
+            for run in N.merge_run_lengths(code, ipt):
+                yield m, ipt, run
+
+
+@pytest.mark.parametrize("method,ipt,run", list(merge_cases()))
+def test_merge_runs_match_oracle(ns, method, ipt, run):
+    """Input sorted in runs of `run` by the oracle; the output must be the
+    oracle's sort of each run of 2 run (several tiles, ragged end)."""
+    n = 3 * 512 * ipt + 777
+    bits = inputs.counter_u32(16, ipt, 0, n)
+    bits[::3] = bits[::3] % 61
+    bits[5::97] = 0xFFFFFFFF
+    x = dev(oracle_runs(bits, run))
+    out = torch.empty_like(x)
+    rc = ns.nsort_merge_runs(x, out, n, run, MERGERS[method], ipt, 0)
+    assert rc == ns.OK, ns.lib().nsort_last_error()
+    np.testing.assert_array_equal(host(out), oracle_runs(bits, 2 * run))
+
+
+@pytest.mark.parametrize("method", list(MERGERS))
+@pytest.mark.parametrize("n", [1, 7, 600, 20000])
+def test_merge_runs_in_place_short_inputs(ns, method, n):
+    ipt, run = 8, 16
+    bits = inputs.counter_u32(17, n, 0, n)
+    buf = dev(np.concatenate([np.zeros(1, np.uint32), oracle_runs(bits, run)]))
+    x = buf[1:]
+    rc = ns.nsort_merge_runs(x, x, n, run, MERGERS[method], ipt, 0)
+    assert rc == ns.OK, ns.lib().nsort_last_error()
+    np.testing.assert_array_equal(host(x), oracle_runs(bits, 2 * run))

@@ -144,3 +144,17 @@ def test_ablation_argument_validation_needs_no_gpu(lib):
     assert nsort.nsort_runs(0x1000, 0x1000, 1 << 41, nsort.NET_BEST, 16, 16, 0) == nsort.EINVAL
     assert nsort.nsort_runs(0, 0, 100, nsort.NET_BEST, 16, 16, 0) == nsort.EINVAL
     assert nsort.nsort_runs(0, 0, 0, nsort.NET_BEST, 16, 8192, 0) == nsort.OK
+
+
+def test_merge_runs_argument_validation_needs_no_gpu(lib):
+    H, S, R = nsort.MERGE_HYBRID, nsort.MERGE_SHUFFLE, nsort.MERGE_SERIAL
+    bad = [(100, 8, H, 16), (100, 512, H, 16), (100, 24, S, 16), (100, 512, S, 16),
+           (100, 4, R, 16), (100, 8192, R, 16), (100, 16, 3, 16), (100, 16, H, 12),
+           (100, 0, S, 16), (1 << 41, 16, H, 16)]
+    for n, run, m, ipt in bad:
+        assert nsort.nsort_merge_runs(0x1000, 0x1000, n, run, m, ipt, 0) == nsort.EINVAL, (run, m)
+    assert nsort.nsort_merge_runs(0, 0, 0, 16, H, 16, 0) == nsort.OK
+    assert nsort.nsort_merge_runs(0, 0x1000, 10, 16, H, 16, 0) == nsort.EINVAL
+    assert nsort.merge_run_lengths(H, 16) == [16, 32, 64, 128, 256]
+    assert nsort.merge_run_lengths(S, 4) == [1, 2, 4, 8, 16, 32, 64]
+    assert nsort.merge_run_lengths(R, 4)[0] == 2 and nsort.merge_run_lengths(R, 4)[-1] == 1024
