@@ -9,7 +9,8 @@ Two parts:
 * ``oracle.c`` (loaded here through ctypes): the plain definition of what the
   method computes — a stable ascending sort of 32-bit keys (paper Sec. 2.1),
   written as a textbook bottom-up merge sort, plus the order-preserving key
-  map for int32 / float32 keys (IEEE 754-2008 totalOrder for float32).
+  map for int32 / float32 keys (IEEE 754-2008 totalOrder for float32), and
+  the same for 64-bit keys (uint64 / int64 / float64).
 * ``networks.py``: the comparator networks the paper compares in Table 1
   (bitonic, odd-even, the 60-comparator 16-input network) and the merging
   networks of Sec. 2.4, as data, with an exhaustive 0-1-principle verifier.
@@ -33,6 +34,7 @@ _BUILD_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD_DIR, "liboracle.so")
 
 DTYPES = {"u32": 0, "i32": 1, "f32": 2}
+DTYPES64 = {"u64": 3, "i64": 4, "f64": 5}
 
 _lock = threading.Lock()
 _lib = None
@@ -61,6 +63,19 @@ def _dt(dtype: str) -> int:
     if dtype not in DTYPES:
         raise ValueError(f"unknown key dtype {dtype!r}; expected one of {sorted(DTYPES)}")
     return DTYPES[dtype]
+
+
+def _dt64(dtype: str) -> int:
+    if dtype not in DTYPES64:
+        raise ValueError(f"unknown 64-bit key dtype {dtype!r}; expected one of {sorted(DTYPES64)}")
+    return DTYPES64[dtype]
+
+
+def _u64(a) -> np.ndarray:
+    a = np.ascontiguousarray(a)
+    if a.dtype.itemsize != 8:
+        raise TypeError(f"expected a 64-bit array, got {a.dtype}")
+    return a.view(np.uint64)
 
 
 def _u32(a) -> np.ndarray:
@@ -92,6 +107,13 @@ class Oracle:
         lib.orc_sort_segmented.argtypes = [u32p, u32p, u32p, u32p, i64p,
                                            ctypes.c_uint64, ctypes.c_int]
         lib.orc_sort_segmented.restype = ctypes.c_int
+        u64p = ctypes.POINTER(ctypes.c_uint64)
+        lib.orc_key64.argtypes = [ctypes.c_uint64, ctypes.c_int]
+        lib.orc_key64.restype = ctypes.c_uint64
+        lib.orc_key64_array.argtypes = [u64p, u64p, ctypes.c_uint64, ctypes.c_int]
+        lib.orc_key64_array.restype = None
+        lib.orc_sort_keys64.argtypes = [u64p, u64p, ctypes.c_uint64, ctypes.c_int]
+        lib.orc_sort_keys64.restype = ctypes.c_int
         self.lib = lib
         self.path = path
 
@@ -109,6 +131,24 @@ class Oracle:
         rc = self.lib.orc_sort_keys(_p(b), _p(out), b.size, _dt(dtype))
         if rc != 0:
             raise RuntimeError(f"orc_sort_keys failed ({rc})")
+        return out
+
+    def key64(self, bits, dtype: str) -> np.ndarray:
+        """The order-preserving unsigned key of each 64-bit pattern."""
+        b = _u64(np.atleast_1d(bits))
+        out = np.empty_like(b)
+        self.lib.orc_key64_array(_p(b, ctypes.c_uint64), _p(out, ctypes.c_uint64), b.size,
+                                 _dt64(dtype))
+        return out
+
+    def sort_keys64(self, bits, dtype: str) -> np.ndarray:
+        """The input 64-bit patterns (uint64 view) in ascending key order."""
+        b = _u64(bits)
+        out = np.empty_like(b)
+        rc = self.lib.orc_sort_keys64(_p(b, ctypes.c_uint64), _p(out, ctypes.c_uint64), b.size,
+                                      _dt64(dtype))
+        if rc != 0:
+            raise RuntimeError(f"orc_sort_keys64 failed ({rc})")
         return out
 
     def sort_pairs(self, bits, vals, dtype: str):
@@ -168,3 +208,11 @@ def sort_pairs(bits, vals, dtype: str):
 
 def sort_segmented(bits, offsets, dtype: str, vals=None):
     return default().sort_segmented(bits, offsets, dtype, vals)
+
+
+def key64(bits, dtype: str) -> np.ndarray:
+    return default().key64(bits, dtype)
+
+
+def sort_keys64(bits, dtype: str) -> np.ndarray:
+    return default().sort_keys64(bits, dtype)

@@ -151,6 +151,80 @@ def keys(n: int, dtype: str = "u32", dist: str = "uniform", seed: int = 0,
     return out
 
 
+KEY64_DTYPES = ("u64", "i64", "f64")
+DISTRIBUTIONS64 = ("uniform", "sorted", "reverse", "dup16", "specials")
+
+# IEEE binary64 specials: -0, +0, +Inf, -Inf, +qNaN, -qNaN, +sNaN,
+# smallest subnormal, -DBL_MAX
+SPECIALS_F64 = np.array([0x8000000000000000, 0x0000000000000000, 0x7FF0000000000000,
+                         0xFFF0000000000000, 0x7FF8000000000000, 0xFFF8000000000000,
+                         0x7FF0000000000001, 0x0000000000000001, 0xFFEFFFFFFFFFFFFF],
+                        dtype=np.uint64)
+
+
+def _int64_bits_to_dtype(bits: np.ndarray, dtype: str) -> np.ndarray:
+    """64-bit draws to key patterns: u64 / i64 the draw itself; f64 the draw
+    read as an int64, converted to float64 and scaled by 2^-63 (U[-1, 1))."""
+    if dtype in ("u64", "i64"):
+        return bits.astype(np.uint64, copy=False)
+    if dtype == "f64":
+        return (bits.view(np.int64).astype(np.float64) * (2.0 ** -63)).view(np.uint64)
+    raise ValueError(f"unknown 64-bit key dtype {dtype!r}")
+
+
+def keys64(n: int, dtype: str = "u64", dist: str = "uniform", seed: int = 0) -> np.ndarray:
+    """n 64-bit key patterns (uint64) of the given dtype and distribution.
+
+    uniform  : one 64-bit draw per element (float64: U[-1, 1)).
+    sorted   : ascending in the dtype's order without a sorting step: element
+               i is i * floor(2^64 / n) plus a draw below that step (signed
+               order for i64, then scaled for f64).
+    reverse  : the sorted sequence, last element first.
+    dup16    : 16 values drawn as for uniform; each element picks one.
+    specials : uniform, with about 1/1000 of the positions replaced by one
+               of SPECIALS_F64 (f64) or by 0, 1, 2^63 - 1, 2^63, 2^64 - 1
+               (u64 / i64), chosen by draw(S_SPECIAL, i).
+    """
+    if dtype not in KEY64_DTYPES:
+        raise ValueError(f"unknown 64-bit key dtype {dtype!r}")
+    if dist not in DISTRIBUTIONS64:
+        raise ValueError(f"unknown distribution {dist!r}")
+    out = np.empty(n, dtype=np.uint64)
+    if n == 0:
+        return out
+    edges = np.array([0, 1, 0x7FFFFFFFFFFFFFFF, 0x8000000000000000, 0xFFFFFFFFFFFFFFFF],
+                     dtype=np.uint64)
+    table = _int64_bits_to_dtype(counter_u64(seed, S_DUP, 0, 16), dtype)
+    step = np.uint64(min((1 << 64) // n, (1 << 64) - 1))
+    for lo in range(0, n, CHUNK):
+        hi = min(n, lo + CHUNK)
+        if dist in ("uniform", "specials"):
+            v = _int64_bits_to_dtype(counter_u64(seed, S_KEYS, lo, hi), dtype)
+            if dist == "specials":
+                h = counter_u64(seed, S_SPECIAL, lo, hi)
+                sp = (h % np.uint64(1000)) == np.uint64(0)
+                sel = h >> np.uint64(40)
+                if dtype == "f64":
+                    rep = SPECIALS_F64[(sel % np.uint64(SPECIALS_F64.size)).astype(np.int64)]
+                else:
+                    rep = edges[(sel % np.uint64(edges.size)).astype(np.int64)]
+                v = np.where(sp, rep, v)
+            out[lo:hi] = v
+        elif dist in ("sorted", "reverse"):
+            if dist == "sorted":
+                i = np.arange(lo, hi, dtype=np.uint64)
+            else:
+                i = np.uint64(n - 1) - np.arange(lo, hi, dtype=np.uint64)
+            with np.errstate(over="ignore"):
+                v = i * step + counter_u64(seed, S_KEYS, lo, hi) % max(step, np.uint64(1))
+            if dtype in ("i64", "f64"):
+                v = v ^ np.uint64(0x8000000000000000)   # ascending in signed order
+            out[lo:hi] = _int64_bits_to_dtype(v, dtype)
+        else:   # dup16
+            out[lo:hi] = table[counter_u32(seed, S_PICK, lo, hi) & np.uint32(15)]
+    return out
+
+
 # IEEE binary32 specials used by the stable-pairs workload
 SPECIALS_F32 = np.array([0x80000000, 0x00000000, 0x7F800000, 0xFF800000,
                          0x7FC00000, 0xFFC00000, 0x7F800001], dtype=np.uint32)

@@ -241,6 +241,119 @@ def test_segmented_matches_per_segment_and_rejects_bad_offsets():
         oracle.sort_segmented(x, np.array([0, 600, 500, 1000], np.int64), "f32")
 
 
+# --- 64-bit keys -------------------------------------------------------------
+
+def f64_less_nonnan(a_bits, b_bits):
+    """IEEE order of two non-NaN binary64 values by numpy comparison, with
+    -0 below +0 (totalOrder)."""
+    a = np.uint64(a_bits).view(np.float64)
+    b = np.uint64(b_bits).view(np.float64)
+    if a == b:
+        return bool(np.signbit(a)) and not bool(np.signbit(b))
+    return bool(a < b)
+
+
+LESS64 = {
+    "u64": lambda a, b: int(a) < int(b),
+    "i64": lambda a, b: int(np.uint64(a).view(np.int64)) < int(np.uint64(b).view(np.int64)),
+    "f64": f64_less_nonnan,
+}
+
+ALPHABET64 = {
+    "u64": [0x0, 0x7, 0x8000000000000000, 0xFFFFFFFFFFFFFFFF],
+    "i64": [0x8000000000000000, 0xFFFFFFFFFFFFFFFF, 0x0, 0x7FFFFFFFFFFFFFFF],   # min, -1, 0, max
+    "f64": [0xBFF8000000000000, 0x8000000000000000, 0x0, 0x4000000000000000],   # -1.5, -0, +0, 2
+}
+
+
+def f64_edge_patterns():
+    """Every sign x exponent edge x mantissa edge combination of binary64."""
+    exps = [0, 1, 2, 1022, 1023, 1024, 2045, 2046, 2047]
+    mants = [0, 1, 2, (1 << 51) - 1, 1 << 51, (1 << 51) + 1, (1 << 52) - 1]
+    out = [(sg << 63) | (e << 52) | m for sg in (0, 1) for e in exps for m in mants]
+    return np.array(out, dtype=np.uint64)
+
+
+def test_key64_u64_identity_and_i64_signed_order():
+    x = inputs.keys64(4096, "u64", "specials", seed=3)
+    np.testing.assert_array_equal(oracle.key64(x, "u64"), x)
+    edges = np.array([-(1 << 63), -2, -1, 0, 1, (1 << 63) - 1], dtype=np.int64)
+    v = np.concatenate([x.view(np.int64), edges])
+    k = oracle.key64(v.view(np.uint64), "i64")
+    order_k = np.argsort(k, kind="stable")
+    order_v = np.argsort(v, kind="stable")
+    np.testing.assert_array_equal(v[order_k], v[order_v])
+
+
+def test_key64_f64_golden_total_order(golden):
+    rows = golden("f64_total_order.txt")
+    bits = np.array([int(r[0], 16) for r in rows], dtype=np.uint64)
+    k = oracle.key64(bits, "f64")
+    assert np.all(k[1:] > k[:-1])
+
+
+def test_key64_f64_matches_float_compare_without_nan():
+    pats = np.concatenate([f64_edge_patterns(), inputs.keys64(2000, "f64", "uniform", seed=4)])
+    f = pats.view(np.float64)
+    pats = pats[~np.isnan(f)]
+    k = oracle.key64(pats, "f64")
+    # sort by (value, sign) with numpy, then the keys must be strictly increasing
+    f = pats.view(np.float64)
+    order = np.lexsort((~np.signbit(f), f))
+    ks = k[order]
+    uniq = np.unique(pats).size == pats.size
+    assert uniq
+    assert np.all(ks[1:] > ks[:-1])
+
+
+def test_key64_f64_nans_beyond_the_infinities():
+    pats = f64_edge_patterns()
+    f = pats.view(np.float64)
+    k = oracle.key64(pats, "f64")
+    kninf = oracle.key64(np.array([0xFFF0000000000000], np.uint64), "f64")[0]
+    kpinf = oracle.key64(np.array([0x7FF0000000000000], np.uint64), "f64")[0]
+    nan = np.isnan(f)
+    neg = np.signbit(f)
+    assert np.all(k[nan & neg] < kninf)
+    assert np.all(k[nan & ~neg] > kpinf)
+
+
+@pytest.mark.parametrize("dtype", list(ALPHABET64))
+def test_sort64_all_words_against_insertion_sort(dtype):
+    less = LESS64[dtype]
+    for n in range(0, 7):
+        for word in itertools.product(ALPHABET64[dtype], repeat=n):
+            bits = np.array(word, dtype=np.uint64)
+            want = insertion_sort_pairs(list(word), less)
+            np.testing.assert_array_equal(oracle.sort_keys64(bits, dtype),
+                                          np.array(want, dtype=np.uint64))
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 17, 1000, 65537])
+def test_sort64_matches_numpy(n):
+    x = inputs.keys64(n, "u64", "uniform", seed=n)
+    np.testing.assert_array_equal(oracle.sort_keys64(x, "u64"), np.sort(x))
+    np.testing.assert_array_equal(oracle.sort_keys64(x, "i64").view(np.int64),
+                                  np.sort(x.view(np.int64)))
+    f = inputs.keys64(n, "f64", "uniform", seed=n)      # no NaN, no -0
+    np.testing.assert_array_equal(oracle.sort_keys64(f, "f64").view(np.float64),
+                                  np.sort(f.view(np.float64)))
+
+
+@pytest.mark.parametrize("dtype", ["u64", "i64", "f64"])
+@pytest.mark.parametrize("dist", ["uniform", "sorted", "reverse", "dup16", "specials"])
+def test_sort64_invariants_and_closed_forms(dtype, dist):
+    x = inputs.keys64(20000, dtype, dist, seed=5)
+    out = oracle.sort_keys64(x, dtype)
+    k = oracle.key64(out, dtype)
+    assert np.all(k[1:] >= k[:-1])                                    # non-decreasing
+    np.testing.assert_array_equal(np.sort(out), np.sort(x))           # a permutation
+    if dist == "sorted":
+        np.testing.assert_array_equal(out, x)                         # identity
+    if dist == "reverse" and np.unique(x).size == x.size:
+        np.testing.assert_array_equal(out, x[::-1])                   # reversal
+
+
 # --- planted mistakes -------------------------------------------------------
 
 MUTATIONS = {
@@ -257,6 +370,18 @@ MUTATIONS = {
     # off-by-one in the run width
     "run_width": (r"uint64_t mid = lo \+ width < n \? lo \+ width : n;",
                   "uint64_t mid = lo + width + 1 < n ? lo + width + 1 : n;"),
+    # 64-bit float map without the complement of negatives
+    "f64_negatives": (r"if \(bits & sign\)\n            return ~bits;",
+                      "if (bits & sign)\n            return bits;"),
+    # 64-bit signed map without the sign flip
+    "i64_sign": (r"return bits \^ sign;\n    if \(dtype == ORC_F64\)",
+                 "return bits;\n    if (dtype == ORC_F64)"),
+    # 64-bit merge drops the left run's tail
+    "lost_tail64": (r"while \(i < mid\)\n        dst\[o\+\+\] = src\[i\+\+\];",
+                    "while (0)\n        dst[o++] = src[i++];"),
+    # 64-bit merge takes from the wrong run
+    "merge64_order": (r"if \(orc_key64\(src\[j\], dtype\) < orc_key64\(src\[i\], dtype\)\)",
+                      "if (orc_key64(src[j], dtype) > orc_key64(src[i], dtype))"),
 }
 
 
@@ -278,6 +403,15 @@ def _pins(orc):
     perm = np.argsort(d, kind="stable")
     if not (np.array_equal(ko, d[perm]) and np.array_equal(vo, v[perm])):
         failed.append("stable_pairs")
+    y = inputs.keys64(5000, "u64", "uniform", seed=1)
+    if not np.array_equal(orc.sort_keys64(y, "u64"), np.sort(y)):
+        failed.append("numpy_u64")
+    if not np.array_equal(orc.sort_keys64(y, "i64").view(np.int64), np.sort(y.view(np.int64))):
+        failed.append("numpy_i64")
+    b64 = np.array([0xBFF0000000000000, 0x8000000000000000, 0x0, 0x3FF0000000000000], np.uint64)
+    k64 = orc.key64(b64, "f64")
+    if not np.all(k64[1:] > k64[:-1]):
+        failed.append("f64_table")
     return failed
 
 
