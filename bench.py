@@ -325,8 +325,9 @@ def time_sort(nsort, torch, fn, reps: int = 5, warm: int = 2):
 
 def bench_configs(nsort, torch):
     """The other plain-sort configurations: 2^28 int32 / float32 keys over
-    several distributions, and 2^27 stable float32 key / uint32 value pairs
-    (Normal(0,1) with 0.1% IEEE specials, payload = index)."""
+    several distributions, 2^27 stable float32 key / uint32 value pairs
+    (Normal(0,1) with 0.1% IEEE specials, payload = index), and 2^27 64-bit
+    keys."""
     from paper_2409_03970_gb300 import inputs
     n = 1 << 28
     out = {}
@@ -355,6 +356,47 @@ def bench_configs(nsort, torch):
     out["pairs_f32_normal_specials_2e27"] = {
         "ms": ms, "gpairs_s": m / ms / 1e6, "passes": passes,
         "hbm_roofline_frac": passes * 16 * m / (ms / 1e3) / 1e9 / load_peaks()["hbm_gbs"]}
+    del kt, vt, kout, vout, tmp
+    torch.cuda.empty_cache()
+    out.update(bench_keys64(nsort, torch))
+    return out
+
+
+def bench_keys64(nsort, torch):
+    """64-bit keys (the wider-key variant): 2^27 uint64 / int64 / float64 keys
+    (1 GiB), 16 B per key per pass; the merge pass's own roofline from its
+    traced launches."""
+    from paper_2409_03970_gb300 import inputs
+    m = 1 << 27
+    peak = load_peaks()["hbm_gbs"]
+    tmp = nsort.scratch(nsort.KIND_KEYS, m, dtype=nsort.U64)
+    ko = torch.empty(m, dtype=torch.int64, device="cuda")
+    passes, _, _ = nsort.nsort_plan(nsort.KIND_KEYS, m, nsort.U64)
+    codes = {"u64": nsort.U64, "i64": nsort.I64, "f64": nsort.F64}
+    out = {}
+    for dt, dist in (("u64", "uniform"), ("i64", "uniform"), ("f64", "uniform"),
+                     ("f64", "specials")):
+        x = torch.from_numpy(inputs.keys64(m, dt, dist, seed=0).view(np.int64)).cuda()
+        code = codes[dt]
+        nsort.nsort_trace_enable(True)
+        ms = time_sort(nsort, torch,
+                       lambda: nsort.nsort_keys(x, ko, m, code, tmp, tmp.numel()))
+        tr = nsort.nsort_trace_read()
+        nsort.nsort_trace_enable(False)
+        r = {"ms": ms, "gkeys_s": m / ms / 1e6, "passes": passes,
+             "hbm_roofline_frac": passes * 16 * m / (ms / 1e3) / 1e9 / peak}
+        mk = tr.get("merge_keys64")
+        if mk and mk["launches"]:
+            lms = mk["total_ms"] / mk["launches"]
+            r["merge_keys64_ms"] = lms
+            r["merge_keys64_frac"] = 16 * m / (lms / 1e3) / 1e9 / peak
+        ts = tr.get("tile_sort_keys64")
+        if ts and ts["launches"]:
+            r["tile_sort_keys64_ms"] = ts["total_ms"] / ts["launches"]
+        out[f"keys_{dt}_{dist}_2e27"] = r
+        del x
+    del tmp, ko
+    torch.cuda.empty_cache()
     return out
 
 

@@ -16,7 +16,8 @@
  *    (allocated with cudaMalloc, torch, ...).  The library allocates no
  *    device memory in nsort_keys / nsort_pairs / nsort_segmented: scratch
  *    comes from the caller's d_tmp of at least nsort_temp_bytes() bytes.
- *  - Keys are 32-bit patterns of type `dtype` (nsort_dtype).  They are
+ *  - Keys are 32-bit patterns of type `dtype` (nsort_dtype), or 64-bit
+ *    patterns for the 64-bit dtypes (nsort_keys only).  They are
  *    ordered by an order-preserving map to unsigned integers: identity for
  *    NSORT_U32, sign-bit flip for NSORT_I32, and for NSORT_F32 the IEEE
  *    754-2008 totalOrder (-NaN < -Inf < ... < -0 < +0 < ... < +Inf < +NaN,
@@ -28,7 +29,8 @@
  *    keys; pair sorts are stable (equal keys keep input order), so the
  *    payload order is determined too.
  *  - in == out is allowed (in-place sort).  d_tmp must not overlap any
- *    input or output.  Pointers need only 4-byte alignment; 16-byte aligned
+ *    input or output.  Pointers need only 4-byte (64-bit keys: 8-byte)
+ *    alignment; 16-byte aligned
  *    buffers take the vectorised path.
  *  - The output (and d_tmp) are working space until the call's work on the
  *    stream is complete: other work must not read or write them meanwhile,
@@ -52,7 +54,12 @@
 extern "C" {
 #endif
 
-typedef enum { NSORT_U32 = 0, NSORT_I32 = 1, NSORT_F32 = 2 } nsort_dtype;
+typedef enum {
+    NSORT_U32 = 0, NSORT_I32 = 1, NSORT_F32 = 2,
+    /* 64-bit keys, nsort_keys only: the same maps on 64-bit patterns (sign
+     * flip for int64, IEEE totalOrder for binary64); pointers 8-byte aligned */
+    NSORT_U64 = 3, NSORT_I64 = 4, NSORT_F64 = 5
+} nsort_dtype;
 
 typedef enum {
     NSORT_KIND_KEYS = 0,            /* nsort_keys */
@@ -72,23 +79,34 @@ typedef enum {
 } nsort_status;
 
 /* Scratch bytes a call of `kind` needs for n keys (and nseg segments, for
- * the segmented kinds; ignored otherwise).  dtype does not change the size.
+ * the segmented kinds; ignored otherwise).  Only the 64-bit dtypes change
+ * the size (kind KEYS: 8-byte key copies and samples).
  * Returns 0 for a bad kind.  Source: the auxiliary O(N) buffer of the
  * paper's merge stages (Sec. 3.2, last paragraph): one ping-pong copy of the
  * keys (and values), plus the per-tile merge-path splitters. */
 size_t nsort_temp_bytes(int kind, uint64_t n, uint64_t nseg, int dtype);
 
-/* Number of passes over the data for a plain sort of n keys (kind KEYS or
- * PAIRS): one tile sort plus ceil(log2(ceil(n / tile))) global merge passes.
- * Writes the tile sizes through the non-NULL pointers.  Used to compute the
- * algorithmic bytes of a sort (passes x 2 x element bytes x n). */
+/* Number of passes over the data for a plain sort of n 32-bit keys (kind
+ * KEYS or PAIRS): one tile sort plus ceil(log2(ceil(n / tile))) global merge
+ * passes.  Writes the tile sizes through the non-NULL pointers.  Used to
+ * compute the algorithmic bytes of a sort (passes x 2 x element bytes x n). */
 int nsort_plan(int kind, uint64_t n, int *passes, int *sort_tile, int *merge_tile);
 
+/* nsort_plan for keys of `dtype`: 64-bit dtypes (kind KEYS only) sort
+ * 4096-key tiles and merge 1920-key tiles.  NSORT_EINVAL for a bad kind, a
+ * 64-bit dtype with kind PAIRS, or n above 2^40. */
+int nsort_plan_dtype(int kind, uint64_t n, int dtype, int *passes, int *sort_tile,
+                     int *merge_tile);
+
 /* Sorts n keys ascending (paper Sec. 2.1: "the input sequence of the length
- * N").  d_keys_in / d_keys_out: n 32-bit patterns, contiguous.  d_tmp:
+ * N").  d_keys_in / d_keys_out: n 32-bit patterns, contiguous, or n 64-bit
+ * patterns for the 64-bit dtypes (8-byte aligned; the paper's register
+ * width W depends on the key type, Sec. 2.2: 64-bit keys are this library's
+ * wider-key variant of the same sort).  d_tmp:
  * nsort_temp_bytes(NSORT_KIND_KEYS, n, 0, dtype) bytes of device scratch,
- * 256-byte aligned.  Errors: NSORT_EINVAL (NULL pointer with n > 0, bad
- * dtype, n too large), NSORT_ENOMEM (tmp_bytes too small), NSORT_ECUDA. */
+ * 256-byte aligned.  Errors: NSORT_EINVAL (NULL or misaligned pointer with
+ * n > 0, bad dtype, n too large), NSORT_ENOMEM (tmp_bytes too small),
+ * NSORT_ECUDA. */
 int nsort_keys(const void *d_keys_in, void *d_keys_out, uint64_t n, int dtype,
                void *d_tmp, size_t tmp_bytes, void *stream);
 

@@ -32,20 +32,30 @@ namespace nsort {
 
 // Thread t stores its VT consecutive outputs o[] at out[t*VT ...], mapped
 // back to bit patterns by DT_OUT.  Full, 16-byte aligned tiles use 128-bit
-// stores straight from registers; others store element by element.
-template <int VT, int DT_OUT>
-__device__ __forceinline__ void store_run(const uint32_t (&o)[VT], uint32_t *tile_out, int count,
-                                          bool full) {
+// stores straight from registers; others store element by element.  K is
+// the key word (32 or 64 bits).
+template <int VT, int DT_OUT, typename K>
+__device__ __forceinline__ void store_run(const K (&o)[VT], K *tile_out, int count, bool full) {
+  constexpr int EPV = 16 / sizeof(K);   // keys per 128-bit store
   const int e0 = threadIdx.x * VT;
-  uint32_t *out = tile_out + e0;
+  K *out = tile_out + e0;
   if (full) {
 #pragma unroll
-    for (int q = 0; q < VT / 4; ++q) {
+    for (int q = 0; q < VT / EPV; ++q) {
       uint4 v;
-      v.x = from_key(o[4 * q + 0], DT_OUT);
-      v.y = from_key(o[4 * q + 1], DT_OUT);
-      v.z = from_key(o[4 * q + 2], DT_OUT);
-      v.w = from_key(o[4 * q + 3], DT_OUT);
+      if constexpr (EPV == 4) {
+        v.x = from_key(o[4 * q + 0], DT_OUT);
+        v.y = from_key(o[4 * q + 1], DT_OUT);
+        v.z = from_key(o[4 * q + 2], DT_OUT);
+        v.w = from_key(o[4 * q + 3], DT_OUT);
+      } else {
+        const uint64_t lo = from_key(o[2 * q + 0], DT_OUT);
+        const uint64_t hi = from_key(o[2 * q + 1], DT_OUT);
+        v.x = (uint32_t)lo;
+        v.y = (uint32_t)(lo >> 32);
+        v.z = (uint32_t)hi;
+        v.w = (uint32_t)(hi >> 32);
+      }
       reinterpret_cast<uint4 *>(out)[q] = v;
     }
   } else {
@@ -154,6 +164,44 @@ __global__ void __launch_bounds__(NT) tile_sort_pairs_kernel(const uint32_t *kin
     store_keep_in_l2(samp + (base + tid * 16) / SAMPLE, ko[0]);
 }
 
+// Tile sort, 64-bit keys (u64 / i64 / f64): the keys tile sort on 64-bit
+// words, NT * 16 keys per tile, the same networks and merges.  Every
+// SAMPLE-th output key goes to the sample array as for 32-bit keys.
+template <int NT, int DT, bool FINAL>
+__global__ void __launch_bounds__(NT) tile_sort_keys64_kernel(const uint64_t *in, uint64_t *out,
+                                                              int64_t n, uint64_t *samp) {
+  constexpr int TILE = NT * 16;
+  extern __shared__ __align__(16) unsigned char tile64_smem[];   // merge_smem_len<u64>(TILE, 16)
+  uint64_t *s = reinterpret_cast<uint64_t *>(tile64_smem);
+  const int tid = threadIdx.x;
+  const int64_t base = (int64_t)blockIdx.x * TILE;
+  const int count = (int)(n - base < TILE ? n - base : TILE);
+  const bool full = count == TILE && aligned16(in + base) && aligned16(out + base);
+  uint64_t r[16];
+  if (full) {
+    const uint4 *p = reinterpret_cast<const uint4 *>(in + base);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const uint4 v = p[tid + NT * j];
+      r[2 * j + 0] = to_key(((uint64_t)v.y << 32) | v.x, DT);
+      r[2 * j + 1] = to_key(((uint64_t)v.w << 32) | v.z, DT);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+#pragma unroll
+      for (int w = 0; w < 2; ++w) {
+        const int e = 2 * (tid + NT * j) + w;
+        r[2 * j + w] = e < count ? to_key(in[base + e], DT) : ~0ull;
+      }
+    }
+  }
+  sort_tile_in_block<NT, 16, Green16Columns>(r, s);
+  store_run<16, FINAL ? DT : DT_U64>(r, out + base, count, full);
+  if (!FINAL && samp && !(tid & (SAMPLE / 16 - 1)) && tid * 16 < count)
+    store_keep_in_l2(samp + (base + tid * 16) / SAMPLE, r[0]);
+}
+
 // Clamps a tile's A co-ranks so that both slices stay inside their runs and
 // add up to the tile: a0 in [max(0, d0 - lb), min(d0, la)] and a1 in
 // [max(a0, d1 - lb), min(la, a0 + d1 - d0)].  For sorted runs the splitters
@@ -202,8 +250,9 @@ __device__ __forceinline__ PassTile pass_tile(int64_t n, int64_t run, int tile,
 
 // Merge-path splitters of one pass, one thread per output tile: how many
 // elements of its pair's A run precede the tile (stable: A wins ties).
-__global__ void partition_kernel(const uint32_t *__restrict__ src, int64_t n, int64_t run,
-                                 int tile, int64_t num_tiles, int64_t *__restrict__ split) {
+template <typename K>
+__global__ void partition_kernel(const K *__restrict__ src, int64_t n, int64_t run, int tile,
+                                 int64_t num_tiles, int64_t *__restrict__ split) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= num_tiles) return;
   const int64_t out0 = t * tile;
@@ -240,23 +289,23 @@ __device__ __forceinline__ void stage_slices(T *s, const T *__restrict__ src, in
 
 // One merge pass over keys: CTA b produces output tile b.  DT_OUT maps the
 // keys back to bit patterns (last pass only).
-template <int NT, int VT, int DT_OUT>
-__global__ void __launch_bounds__(NT, 6) merge_keys_kernel(const uint32_t *__restrict__ src,
-                                                           uint32_t *__restrict__ dst, int64_t n,
+template <int NT, int VT, int DT_OUT, typename K = uint32_t>
+__global__ void __launch_bounds__(NT, sizeof(K) == 4 ? 6 : 3) merge_keys_kernel(const K *__restrict__ src,
+                                                           K *__restrict__ dst, int64_t n,
                                                            int64_t run,
                                                            const int64_t *__restrict__ split) {
   constexpr int TILE = NT * VT;
-  __shared__ uint32_t s[merge_smem_len<uint32_t>(TILE, VT)];
+  __shared__ K s[merge_smem_len<K>(TILE, VT)];
   const int tid = threadIdx.x;
   const PassTile g = pass_tile(n, run, TILE, split);
   stage_slices<NT, VT>(s, src, g.a_off, g.b_off, g.na, g.count);
   __syncthreads();
   const int diag = tid * VT < g.count ? tid * VT : g.count;
   const int ai = merge_path_smem(s, 0, g.na, g.na, g.nb, diag);
-  uint32_t o[VT];
+  K o[VT];
   int unused[VT];
   serial_merge<VT, false>(s, ai, g.na, g.na + diag - ai, g.count, o, unused);
-  uint32_t *out = dst + g.out0;
+  K *out = dst + g.out0;
   store_run<VT, DT_OUT>(o, out, g.count, g.count == TILE && aligned16(out));
 }
 
@@ -355,10 +404,10 @@ __global__ void partition_pairs_kernel(const uint32_t *__restrict__ src, int64_t
 // searched in that window only, the merge-path conditions are checked at
 // the result, and a full search is done if they fail, so the splitter is
 // exact whatever the samples say.
-__global__ void partition_sampled_kernel(const uint32_t *__restrict__ src,
-                                         const uint32_t *__restrict__ samp, int64_t n,
-                                         int64_t run, int64_t tpp, int tile, int64_t num_tiles,
-                                         int64_t *__restrict__ split) {
+template <typename K>
+__global__ void partition_sampled_kernel(const K *__restrict__ src, const K *__restrict__ samp,
+                                         int64_t n, int64_t run, int64_t tpp, int tile,
+                                         int64_t num_tiles, int64_t *__restrict__ split) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= num_tiles) return;
   const int64_t pair = t / tpp;
@@ -368,8 +417,8 @@ __global__ void partition_sampled_kernel(const uint32_t *__restrict__ src,
   const int64_t rest = n - pair0 - run;
   const int64_t lb = rest <= 0 ? 0 : (rest < run ? rest : run);
   const int64_t d = j * tile;
-  const uint32_t *A = src + pair0;
-  const uint32_t *B = A + la;
+  const K *A = src + pair0;
+  const K *B = A + la;
   const int64_t lo = d - lb > 0 ? d - lb : 0;
   const int64_t hi = d < la ? d : la;
   const int64_t qs = merge_path_global(samp + pair0 / SAMPLE, (la + SAMPLE - 1) / SAMPLE,
@@ -394,45 +443,54 @@ __global__ void partition_sampled_kernel(const uint32_t *__restrict__ src,
 // starts at the 16-byte boundary below a_off, so A[i] is at sh_a + i; the B
 // window starts at the first 16-byte boundary at least SENT elements after
 // A's end, leaving room for the largest-key sentinels of the unchecked
-// serial merge.
+// serial merge.  EPV keys of type K fill 16 bytes.
 constexpr int SENT = 32;
 struct SmemSlices {
   int sh_a, base_b, sh_b;
 };
+template <typename K>
 __device__ __forceinline__ SmemSlices smem_slices(const PairTile &g) {
+  constexpr int EPV = 16 / sizeof(K);
   SmemSlices l;
-  l.sh_a = (int)(g.a_off & 3);
-  l.base_b = (l.sh_a + g.na + SENT + 3) & ~3;
-  l.sh_b = (int)(g.b_off & 3);
+  l.sh_a = (int)(g.a_off & (EPV - 1));
+  l.base_b = (l.sh_a + g.na + SENT + EPV - 1) & ~(EPV - 1);
+  l.sh_b = (int)(g.b_off & (EPV - 1));
   return l;
 }
 
 // Issues the bulk copies of tile g into buf (and, for pairs, of the values
 // into vbuf at the same offsets); lane 0 of warp 0, into buffers no thread
 // is reading.  Each slice's window is rounded out to 16-byte boundaries, so
-// up to 3 elements past a slice land in the gap behind it (overwritten by
-// sentinels, or never read by the bounds-checked merge); windows are
-// clipped at n_al = n & ~3, past which the warps load the at most 3
-// remaining elements themselves.
-__device__ __forceinline__ void issue_tile(const uint32_t *__restrict__ src,
+// up to EPV - 1 elements past a slice land in the gap behind it
+// (overwritten by sentinels, or never read by the bounds-checked merge);
+// windows are clipped at n_al = n rounded down to a multiple of EPV, past
+// which the warps load the at most EPV - 1 remaining elements themselves.
+// Values (pairs, 32-bit keys only) are 32-bit words at the keys' offsets.
+template <typename K>
+__device__ __forceinline__ void issue_tile(const K *__restrict__ src,
                                            const uint32_t *__restrict__ vsrc, int64_t n_al,
-                                           const PairTile &g, uint32_t *buf, uint32_t *vbuf,
+                                           const PairTile &g, K *buf, uint32_t *vbuf,
                                            uint64_t *bar) {
-  const SmemSlices l = smem_slices(g);
-  const int64_t aw0 = g.a_off & ~int64_t(3);
-  int64_t aw1 = (g.a_off + g.na + 3) & ~int64_t(3);
-  const int64_t bw0 = g.b_off & ~int64_t(3);
-  int64_t bw1 = (g.b_off + g.nb + 3) & ~int64_t(3);
+  constexpr int64_t EPV = 16 / sizeof(K);
+  const SmemSlices l = smem_slices<K>(g);
+  const int64_t aw0 = g.a_off & ~(EPV - 1);
+  int64_t aw1 = (g.a_off + g.na + EPV - 1) & ~(EPV - 1);
+  const int64_t bw0 = g.b_off & ~(EPV - 1);
+  int64_t bw1 = (g.b_off + g.nb + EPV - 1) & ~(EPV - 1);
   aw1 = aw1 < n_al ? aw1 : n_al;
   bw1 = bw1 < n_al ? bw1 : n_al;
-  const uint32_t bytes_a = (g.na > 0 && aw1 > aw0) ? (uint32_t)((aw1 - aw0) * 4) : 0u;
-  const uint32_t bytes_b = (g.nb > 0 && bw1 > bw0) ? (uint32_t)((bw1 - bw0) * 4) : 0u;
-  mbar_arrive_expect_tx(bar, (bytes_a + bytes_b) * (vsrc ? 2u : 1u));
+  const uint32_t bytes_a =
+      (g.na > 0 && aw1 > aw0) ? (uint32_t)((aw1 - aw0) * (int64_t)sizeof(K)) : 0u;
+  const uint32_t bytes_b =
+      (g.nb > 0 && bw1 > bw0) ? (uint32_t)((bw1 - bw0) * (int64_t)sizeof(K)) : 0u;
+  const uint32_t vbytes_a = vsrc ? bytes_a / (uint32_t)(sizeof(K) / 4) : 0u;
+  const uint32_t vbytes_b = vsrc ? bytes_b / (uint32_t)(sizeof(K) / 4) : 0u;
+  mbar_arrive_expect_tx(bar, bytes_a + bytes_b + vbytes_a + vbytes_b);
   if (bytes_a) bulk_load(buf, src + aw0, bytes_a, bar);
   if (bytes_b) bulk_load(buf + l.base_b, src + bw0, bytes_b, bar);
   if (vsrc) {
-    if (bytes_a) bulk_load(vbuf, vsrc + aw0, bytes_a, bar);
-    if (bytes_b) bulk_load(vbuf + l.base_b, vsrc + bw0, bytes_b, bar);
+    if (vbytes_a) bulk_load(vbuf, vsrc + aw0, vbytes_a, bar);
+    if (vbytes_b) bulk_load(vbuf + l.base_b, vsrc + bw0, vbytes_b, bar);
   }
 }
 
@@ -447,34 +505,37 @@ __device__ __forceinline__ void issue_tile(const uint32_t *__restrict__ src,
 // gathers the values from shared memory.  Each warp's outputs are
 // contiguous (32 * VT), so each warp stages and bulk-stores its own part
 // with warp-level synchronisation only.  Lane 0 of warp 0 loads the
-// splitters of the tile after next one iteration early.
-template <int NT, int VT, int DT_OUT, bool PAIRS>
+// splitters of the tile after next one iteration early.  K is the key word:
+// 32-bit keys (keys or pairs) or 64-bit keys (keys only).
+template <int NT, int VT, int DT_OUT, bool PAIRS, typename K = uint32_t>
 __global__ void __launch_bounds__(NT, PAIRS ? 3 : 4) merge_tma_kernel(
-    const uint32_t *__restrict__ src, const uint32_t *__restrict__ vsrc,
-    uint32_t *__restrict__ dst, uint32_t *__restrict__ vdst, int64_t n, int64_t run,
-    int64_t tpp, int64_t num_tiles, const int64_t *__restrict__ split, int *status,
-    uint32_t *samp, int reverse) {
+    const K *__restrict__ src, const uint32_t *__restrict__ vsrc, K *__restrict__ dst,
+    uint32_t *__restrict__ vdst, int64_t n, int64_t run, int64_t tpp, int64_t num_tiles,
+    const int64_t *__restrict__ split, int *status, K *samp, int reverse) {
   constexpr int TILE = NT * VT;
   constexpr int WOUT = 32 * VT;                       // outputs per warp
+  constexpr int EPV = 16 / sizeof(K);                 // keys per 16 bytes
   // A window + gap, B window + gap, rounding slack
   constexpr int IN_LEN = (TILE + 2 * SENT + 16) & ~3;
   static_assert(SENT >= (PAIRS ? VT + 2 : VT + 1), "the gap behind each run covers a merge's overrun");
   static_assert(SENT == 32, "one sentinel per lane and slice");
   static_assert(WOUT % 4 == 0, "warp output slices must be 16-byte multiples");
   static_assert(WOUT <= 32 * SAMPLE, "one sample per lane and warp slice");
+  static_assert(!PAIRS || sizeof(K) == 4, "pairs carry 32-bit keys");
   // dynamic shared memory: keys [in 0][in 1] | values [in 0][in 1] | keys out | values out
   extern __shared__ __align__(128) unsigned char tma_smem[];
-  uint32_t(*in_buf)[IN_LEN] = reinterpret_cast<uint32_t(*)[IN_LEN]>(tma_smem);
-  uint32_t(*vin_buf)[IN_LEN] =
-      reinterpret_cast<uint32_t(*)[IN_LEN]>(tma_smem + (PAIRS ? 2 * IN_LEN * 4 : 0));
-  uint32_t *out_buf = reinterpret_cast<uint32_t *>(tma_smem) + (PAIRS ? 4 : 2) * IN_LEN;
-  uint32_t *vout_buf = out_buf + TILE;
+  K(*in_buf)[IN_LEN] = reinterpret_cast<K(*)[IN_LEN]>(tma_smem);
+  uint32_t(*vin_buf)[IN_LEN] = reinterpret_cast<uint32_t(*)[IN_LEN]>(
+      tma_smem + (PAIRS ? 2 * IN_LEN * sizeof(K) : 0));
+  K *out_buf = reinterpret_cast<K *>(tma_smem + (PAIRS ? 2 * IN_LEN * (sizeof(K) + 4)
+                                                        : 2 * IN_LEN * sizeof(K)));
+  uint32_t *vout_buf = reinterpret_cast<uint32_t *>(out_buf + TILE);
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ PairTile desc[2];   // geometry of the tile in each buffer, written by thread 0
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int warp = tid >> 5;
-  const int64_t n_al = n & ~int64_t(3);
+  const int64_t n_al = n & ~int64_t(EPV - 1);
   const int64_t G = gridDim.x;
   int64_t t = blockIdx.x;
   // loop index i -> tile: ascending, or descending when `reverse` (passes
@@ -500,7 +561,7 @@ __global__ void __launch_bounds__(NT, PAIRS ? 3 : 4) merge_tma_kernel(
   }
   __syncthreads();
   bool ok = true;
-  uint32_t *wout = out_buf + warp * WOUT;
+  K *wout = out_buf + warp * WOUT;
   uint32_t *wvout = vout_buf + warp * WOUT;
   for (int it = 0; t < num_tiles; ++it, t += G) {
     const int b = it & 1;
@@ -527,21 +588,21 @@ __global__ void __launch_bounds__(NT, PAIRS ? 3 : 4) merge_tma_kernel(
       }
     }
     const PairTile g = desc[b];
-    const SmemSlices l = smem_slices(g);
-    uint32_t *s = in_buf[b];
+    const SmemSlices l = smem_slices<K>(g);
+    K *s = in_buf[b];
     uint32_t *sv = vin_buf[b];
     const int a0 = l.sh_a, b0 = l.base_b + l.sh_b;
     // this warp's own array-end elements (and sentinels, for keys); the same
     // values in every warp
     if (g.a_off + g.na > n_al || g.b_off + g.nb > n_al) {
-      if (lane < 3) {
+      if (lane < EPV - 1) {
         const int64_t i = (g.a_off > n_al ? g.a_off : n_al) + lane;
         if (i < g.a_off + g.na) {
           s[a0 + (int)(i - g.a_off)] = __ldg(src + i);
           if (PAIRS) sv[a0 + (int)(i - g.a_off)] = __ldg(vsrc + i);
         }
-      } else if (lane < 6) {
-        const int64_t i = (g.b_off > n_al ? g.b_off : n_al) + (lane - 3);
+      } else if (lane < 2 * (EPV - 1)) {
+        const int64_t i = (g.b_off > n_al ? g.b_off : n_al) + (lane - (EPV - 1));
         if (i < g.b_off + g.nb) {
           s[b0 + (int)(i - g.b_off)] = __ldg(src + i);
           if (PAIRS) sv[b0 + (int)(i - g.b_off)] = __ldg(vsrc + i);
@@ -549,14 +610,14 @@ __global__ void __launch_bounds__(NT, PAIRS ? 3 : 4) merge_tma_kernel(
       }
     }
     if (!PAIRS) {
-      s[a0 + g.na + lane] = 0xFFFFFFFFu;
-      s[b0 + g.nb + lane] = 0xFFFFFFFFu;
+      s[a0 + g.na + lane] = ~K(0);
+      s[b0 + g.nb + lane] = ~K(0);
     }
     fence_proxy_async_smem();   // ordered before later bulk copies into this buffer
     __syncwarp();
     const int diag = tid * VT < g.count ? tid * VT : g.count;
     const int ai = merge_path_plain(s, a0, g.na, b0, g.nb, diag);
-    uint32_t o[VT];
+    K o[VT];
     int from[VT];
     if (PAIRS) serial_merge_plain<VT, true>(s, a0 + ai, a0 + g.na, b0 + diag - ai, b0 + g.nb, o, from);
     else serial_merge_sentinel<VT>(s, a0 + ai, b0 + diag - ai, o);
@@ -593,13 +654,13 @@ __global__ void __launch_bounds__(NT, PAIRS ? 3 : 4) merge_tma_kernel(
       if (e < wcount) store_keep_in_l2(samp + (gb + e) / SAMPLE, wout[e]);
     }
     if (wcount > 0) {
-      const int body = wcount & ~3;
+      const int body = wcount & ~(EPV - 1);
       if (lane == 0 && body) {
-        bulk_store(dst + g.out0 + w0, wout, (uint32_t)body * 4u);
+        bulk_store(dst + g.out0 + w0, wout, (uint32_t)body * (uint32_t)sizeof(K));
         if (PAIRS) bulk_store(vdst + g.out0 + w0, wvout, (uint32_t)body * 4u);
         bulk_commit();
       }
-      if (lane < (wcount & 3)) {
+      if (lane < (wcount & (EPV - 1))) {
         dst[g.out0 + w0 + body + lane] = wout[body + lane];
         if (PAIRS) vdst[g.out0 + w0 + body + lane] = wvout[body + lane];
       }
@@ -628,13 +689,27 @@ constexpr int TMA_PMERGE_NT = 128;  // pairs: 128 threads x 15 = 1920 outputs
 constexpr int TMA_PMERGE_VT = 15;
 constexpr int TMA_PMERGE_TILE = TMA_PMERGE_NT * TMA_PMERGE_VT;
 
+// 64-bit keys: tiles of 256 x 16 keys; merge tiles of 128 x 15 outputs (the
+// pairs geometry: the same bytes per element); staged-load fallback 256 x 16
+constexpr int KEYS64_SORT_NT = 256;
+constexpr int TMA_K64_NT = 128;
+constexpr int TMA_K64_VT = 15;
+constexpr int TMA_K64_TILE = TMA_K64_NT * TMA_K64_VT;
+constexpr int MERGE64_NT = 256;
+constexpr int MERGE64_VT = 16;
+
 // dynamic shared memory of merge_tma_kernel: input buffers (two per array)
-// and output staging (one per array)
-constexpr size_t tma_merge_smem(int tile, bool pairs) {
-  return sizeof(uint32_t) * ((pairs ? 4 : 2) * ((tile + 2 * 32 + 16) & ~3) + (pairs ? 2 : 1) * tile);
+// and output staging (one per array); key words of kbytes bytes, 32-bit values
+constexpr size_t tma_merge_smem(int tile, bool pairs, size_t kbytes = 4) {
+  return (kbytes + (pairs ? 4 : 0)) * (2 * ((tile + 2 * 32 + 16) & ~3) + tile);
 }
 constexpr size_t TMA_MERGE_SMEM = tma_merge_smem(TMA_MERGE_TILE, false);
 constexpr size_t TMA_PMERGE_SMEM = tma_merge_smem(TMA_PMERGE_TILE, true);
+constexpr size_t TMA_K64_SMEM = tma_merge_smem(TMA_K64_TILE, false, 8);
+constexpr int KEYS64_SORT_TILE = KEYS64_SORT_NT * 16;
+constexpr size_t KEYS64_SORT_SMEM =
+    sizeof(uint64_t) * merge_smem_len<uint64_t>(KEYS64_SORT_TILE, 16);
+constexpr int MERGE64_TILE = MERGE64_NT * MERGE64_VT;
 
 constexpr int KEYS_SORT_TILE = KEYS_SORT_NT * 16;
 constexpr size_t KEYS_SORT_SMEM = sizeof(uint32_t) * merge_smem_len<uint32_t>(KEYS_SORT_TILE, 16);
@@ -656,32 +731,35 @@ int64_t pair_tiles(int64_t n, int64_t run, int tile, int64_t *tpp_out) {
   return full * tpp + (rem + tile - 1) / tile;
 }
 
-Plan make_plan(int kind, uint64_t n) {
+Plan make_plan(int kind, uint64_t n, int dtype) {
   Plan p;
   const bool pairs = kind == NSORT_KIND_PAIRS;
+  const bool wide = !pairs && dtype >= NSORT_U64;   // 64-bit keys
+  const size_t kw = wide ? 8 : 4;                   // bytes per key word
   p.n = (int64_t)n;
-  p.sort_tile = pairs ? PAIRS_SORT_TILE : KEYS_SORT_TILE;
+  p.sort_tile = pairs ? PAIRS_SORT_TILE : (wide ? KEYS64_SORT_TILE : KEYS_SORT_TILE);
   // the bulk-copy pass's tile; the staged-load fallback uses (P)MERGE_TILE
-  p.merge_tile = pairs ? TMA_PMERGE_TILE : TMA_MERGE_TILE;
+  p.merge_tile = pairs ? TMA_PMERGE_TILE : (wide ? TMA_K64_TILE : TMA_MERGE_TILE);
+  const int fallback_tile = pairs ? PMERGE_TILE : (wide ? MERGE64_TILE : MERGE_TILE);
   const int64_t runs = (p.n + p.sort_tile - 1) / p.sort_tile;
   p.merge_passes = 0;
   while ((int64_t(1) << p.merge_passes) < runs) ++p.merge_passes;
-  p.num_merge_tiles = (p.n + (pairs ? PMERGE_TILE : MERGE_TILE) - 1) / (pairs ? PMERGE_TILE : MERGE_TILE);
+  p.num_merge_tiles = (p.n + fallback_tile - 1) / fallback_tile;
   // splitters: enough for the power-of-two tiling and for the pair-aligned
   // tiling of every pass
   int64_t max_tiles = p.num_merge_tiles;
   for (int pass = 0; pass < p.merge_passes; ++pass) {
-    const int64_t t = pair_tiles(p.n, (int64_t)p.sort_tile << pass,
-                                 pairs ? TMA_PMERGE_TILE : TMA_MERGE_TILE, nullptr);
+    const int64_t t = pair_tiles(p.n, (int64_t)p.sort_tile << pass, p.merge_tile, nullptr);
     if (t > max_tiles) max_tiles = t;
   }
-  const size_t kb = align_up((size_t)n * 4, 256);
+  const size_t kb = align_up((size_t)n * kw, 256);
+  const size_t vb = align_up((size_t)n * 4, 256);
   p.status_off = 0;
   p.keys_off = 256;
   p.vals_off = p.keys_off + kb;
-  p.split_off = pairs ? p.vals_off + kb : p.keys_off + kb;
+  p.split_off = pairs ? p.vals_off + vb : p.keys_off + kb;
   p.samp_off = p.split_off + align_up((size_t)(max_tiles + 1) * sizeof(int64_t), 256);
-  p.total = p.merge_passes == 0 ? 0 : p.samp_off + align_up((size_t)(n / SAMPLE + 2) * 4, 256);
+  p.total = p.merge_passes == 0 ? 0 : p.samp_off + align_up((size_t)(n / SAMPLE + 2) * kw, 256);
   return p;
 }
 
@@ -797,16 +875,29 @@ static void tma_merge_attrs(size_t smem) {
   }
 }
 
-// Persistent merge pass: SMs x resident CTAs, found once per device and kind.
-static int tma_merge_grid(int64_t tiles, bool pairs) {
-  static std::atomic<int> cached[2][64];
+// Persistent merge pass: SMs x resident CTAs, found once per device and
+// kind (0 keys, 1 pairs, 2 64-bit keys).
+static int tma_merge_grid(int64_t tiles, int kind) {
+  static std::atomic<int> cached[3][64];
   int dev = 0;
   cudaGetDevice(&dev);
-  int g = dev < 64 ? cached[pairs][dev].load() : 0;
+  int g = dev < 64 ? cached[kind][dev].load() : 0;
   if (g == 0) {
     int sms = 0, occ = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (pairs) {
+    if (kind == 2) {
+      const void *fns[3] = {
+          (const void *)merge_tma_kernel<TMA_K64_NT, TMA_K64_VT, DT_U64, false, uint64_t>,
+          (const void *)merge_tma_kernel<TMA_K64_NT, TMA_K64_VT, DT_I64, false, uint64_t>,
+          (const void *)merge_tma_kernel<TMA_K64_NT, TMA_K64_VT, DT_F64, false, uint64_t>};
+      for (const void *f : fns) {
+        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TMA_K64_SMEM);
+        cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      }
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &occ, merge_tma_kernel<TMA_K64_NT, TMA_K64_VT, DT_U64, false, uint64_t>, TMA_K64_NT,
+          TMA_K64_SMEM);
+    } else if (kind == 1) {
       tma_merge_attrs<TMA_PMERGE_NT, TMA_PMERGE_VT, true>(TMA_PMERGE_SMEM);
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(
           &occ, merge_tma_kernel<TMA_PMERGE_NT, TMA_PMERGE_VT, DT_U32, true>, TMA_PMERGE_NT,
@@ -818,7 +909,7 @@ static int tma_merge_grid(int64_t tiles, bool pairs) {
           TMA_MERGE_SMEM);
     }
     g = (sms > 0 ? sms : 1) * (occ > 0 ? occ : 1);
-    if (dev < 64) cached[pairs][dev].store(g);
+    if (dev < 64) cached[kind][dev].store(g);
   }
   return (int)(tiles < g ? tiles : g);
 }
@@ -839,7 +930,7 @@ static void launch_merge_tma(const uint32_t *src, const uint32_t *vsrc, uint32_t
     partition_sampled_kernel<<<(unsigned)((tiles + 255) / 256), 256, 0, st>>>(
         src, samp_in, n, run, tpp, tile, tiles, split);
   }
-  const unsigned grid = (unsigned)tma_merge_grid(tiles, pairs);
+  const unsigned grid = (unsigned)tma_merge_grid(tiles, pairs ? 1 : 0);
   TraceScope tr(pairs ? TK_MERGE_PAIRS : TK_MERGE_KEYS, st);
 #define NSORT_MT(NT, VT, DT, P, SMEM)                                                      \
   merge_tma_kernel<NT, VT, DT, P><<<grid, NT, SMEM, st>>>(src, vsrc, dst, vdst, n, run, tpp, \
@@ -854,6 +945,99 @@ static void launch_merge_tma(const uint32_t *src, const uint32_t *vsrc, uint32_t
     else NSORT_MT(TMA_PMERGE_NT, TMA_PMERGE_VT, DT_F32, true, TMA_PMERGE_SMEM);
   }
 #undef NSORT_MT
+}
+
+// ---- 64-bit keys -------------------------------------------------------------
+
+static void launch_tile_sort_keys64(const uint64_t *in, uint64_t *out, int64_t n, int dt,
+                                    bool final_pass, unsigned grid, uint64_t *samp,
+                                    cudaStream_t st) {
+  static_assert(KEYS64_SORT_SMEM <= 48 * 1024, "fits the default dynamic shared memory");
+#define NSORT_TSK64(DT, FIN)                                                            \
+  tile_sort_keys64_kernel<KEYS64_SORT_NT, DT, FIN><<<grid, KEYS64_SORT_NT, KEYS64_SORT_SMEM, \
+                                                     st>>>(in, out, n, samp)
+  if (dt == DT_U64) { if (final_pass) NSORT_TSK64(DT_U64, true); else NSORT_TSK64(DT_U64, false); }
+  else if (dt == DT_I64) { if (final_pass) NSORT_TSK64(DT_I64, true); else NSORT_TSK64(DT_I64, false); }
+  else { if (final_pass) NSORT_TSK64(DT_F64, true); else NSORT_TSK64(DT_F64, false); }
+#undef NSORT_TSK64
+}
+
+// One bulk-copy merge pass over 64-bit keys (sampled partition, then the
+// persistent merge), as launch_merge_tma does for 32-bit keys.
+static void launch_merge_tma64(const uint64_t *src, uint64_t *dst, int64_t n, int64_t run,
+                               int64_t *split, int *status, int dt_out, const uint64_t *samp_in,
+                               uint64_t *samp_out, int reverse, cudaStream_t st) {
+  int64_t tpp = 0;
+  const int64_t tiles = pair_tiles(n, run, TMA_K64_TILE, &tpp);
+  {
+    TraceScope tr(TK_PARTITION, st);
+    partition_sampled_kernel<<<(unsigned)((tiles + 255) / 256), 256, 0, st>>>(
+        src, samp_in, n, run, tpp, TMA_K64_TILE, tiles, split);
+  }
+  const unsigned grid = (unsigned)tma_merge_grid(tiles, 2);
+  TraceScope tr(TK_MERGE_KEYS64, st);
+#define NSORT_MT64(DT)                                                                      \
+  merge_tma_kernel<TMA_K64_NT, TMA_K64_VT, DT, false, uint64_t>                             \
+      <<<grid, TMA_K64_NT, TMA_K64_SMEM, st>>>(src, nullptr, dst, nullptr, n, run, tpp, tiles, \
+                                               split, status, samp_out, reverse)
+  if (dt_out == DT_U64) NSORT_MT64(DT_U64);
+  else if (dt_out == DT_I64) NSORT_MT64(DT_I64);
+  else NSORT_MT64(DT_F64);
+#undef NSORT_MT64
+}
+
+// Staged-load merge pass over 64-bit keys, for output buffers that are not
+// 16-byte aligned.
+static void launch_merge_staged64(const uint64_t *src, uint64_t *dst, int64_t n, int64_t run,
+                                  int64_t *split, int dt_out, int64_t tiles, cudaStream_t st) {
+  {
+    TraceScope tr(TK_PARTITION, st);
+    partition_kernel<<<(unsigned)((tiles + 255) / 256), 256, 0, st>>>(src, n, run, MERGE64_TILE,
+                                                                     tiles, split);
+  }
+  TraceScope tr(TK_MERGE_KEYS64, st);
+#define NSORT_MK64(DT)                                                                   \
+  merge_keys_kernel<MERGE64_NT, MERGE64_VT, DT, uint64_t><<<(unsigned)tiles, MERGE64_NT, 0, \
+                                                           st>>>(src, dst, n, run, split)
+  if (dt_out == DT_U64) NSORT_MK64(DT_U64);
+  else if (dt_out == DT_I64) NSORT_MK64(DT_I64);
+  else NSORT_MK64(DT_F64);
+#undef NSORT_MK64
+}
+
+int sort_keys64_impl(const uint64_t *in, uint64_t *out, int64_t n, int dt, void *tmp,
+                     cudaStream_t st) {
+  const Plan p = make_plan(NSORT_KIND_KEYS, (uint64_t)n, dt);
+  char *t = static_cast<char *>(tmp);
+  uint64_t *bufs[2] = {out, p.merge_passes ? reinterpret_cast<uint64_t *>(t + p.keys_off) : nullptr};
+  int64_t *split = p.merge_passes ? reinterpret_cast<int64_t *>(t + p.split_off) : nullptr;
+  int *status = p.merge_passes ? reinterpret_cast<int *>(t + p.status_off) : nullptr;
+  uint64_t *samp = p.merge_passes ? reinterpret_cast<uint64_t *>(t + p.samp_off) : nullptr;
+  if (status && cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess)
+    return launch_status("cudaMemsetAsync");
+  const bool tma = !(reinterpret_cast<uintptr_t>(out) & 15);
+  int cur = p.merge_passes % 2;   // the last pass must land in bufs[0] == out
+  const int64_t tiles = (n + p.sort_tile - 1) / p.sort_tile;
+  {
+    TraceScope tr(TK_TILE_SORT_KEYS64, st);
+    launch_tile_sort_keys64(in, bufs[cur], n, dt, p.merge_passes == 0, (unsigned)tiles,
+                            tma ? samp : nullptr, st);
+  }
+  int rc = launch_status("tile_sort_keys64");
+  for (int pass = 0; rc == NSORT_OK && pass < p.merge_passes; ++pass) {
+    const int64_t run = (int64_t)p.sort_tile << pass;
+    const bool last = pass == p.merge_passes - 1;
+    const int dt_out = last ? dt : DT_U64;
+    if (tma)
+      launch_merge_tma64(bufs[cur], bufs[cur ^ 1], n, run, split, status, dt_out, samp,
+                         last ? nullptr : samp, (pass & 1) == 0, st);
+    else
+      launch_merge_staged64(bufs[cur], bufs[cur ^ 1], n, run, split, dt_out, p.num_merge_tiles,
+                            st);
+    rc = launch_status("merge_keys64");
+    cur ^= 1;
+  }
+  return rc;
 }
 
 // ---- the sorts ------------------------------------------------------------
@@ -953,30 +1137,44 @@ int sort_pairs_impl(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, ui
 
 using namespace nsort;
 
+static bool is_wide(int dtype) {
+  return dtype == NSORT_U64 || dtype == NSORT_I64 || dtype == NSORT_F64;
+}
+
 extern "C" size_t nsort_temp_bytes(int kind, uint64_t n, uint64_t nseg, int dtype) {
-  (void)dtype;
-  if (kind == NSORT_KIND_KEYS || kind == NSORT_KIND_PAIRS) return make_plan(kind, n).total;
+  if (kind == NSORT_KIND_KEYS) return make_plan(kind, n, is_wide(dtype) ? dtype : 0).total;
+  if (kind == NSORT_KIND_PAIRS) return make_plan(kind, n).total;
   return segmented_temp_bytes(kind, n, nseg);
 }
 
-extern "C" int nsort_plan(int kind, uint64_t n, int *passes, int *sort_tile, int *merge_tile) {
+extern "C" int nsort_plan_dtype(int kind, uint64_t n, int dtype, int *passes, int *sort_tile,
+                                int *merge_tile) {
   if (kind != NSORT_KIND_KEYS && kind != NSORT_KIND_PAIRS) return NSORT_EINVAL;
   if (n > MAX_KEYS) return NSORT_EINVAL;
-  const Plan p = make_plan(kind, n);
+  if (is_wide(dtype) && kind != NSORT_KIND_KEYS) return NSORT_EINVAL;
+  const Plan p = make_plan(kind, n, is_wide(dtype) ? dtype : 0);
   if (passes) *passes = 1 + p.merge_passes;
   if (sort_tile) *sort_tile = p.sort_tile;
   if (merge_tile) *merge_tile = p.merge_tile;
   return NSORT_OK;
 }
 
+extern "C" int nsort_plan(int kind, uint64_t n, int *passes, int *sort_tile, int *merge_tile) {
+  return nsort_plan_dtype(kind, n, NSORT_U32, passes, sort_tile, merge_tile);
+}
+
 static int check_common(const void *a, const void *b, uint64_t n, int dtype, void *tmp,
                         size_t tmp_bytes, int kind) {
-  if (dtype != NSORT_U32 && dtype != NSORT_I32 && dtype != NSORT_F32) return NSORT_EINVAL;
+  const bool wide = is_wide(dtype);
+  if (dtype != NSORT_U32 && dtype != NSORT_I32 && dtype != NSORT_F32 && !wide)
+    return NSORT_EINVAL;
+  if (wide && kind != NSORT_KIND_KEYS) return NSORT_EINVAL;
   if (n > MAX_KEYS) return NSORT_EINVAL;
   if (n == 0) return NSORT_OK;
   if (!a || !b) return NSORT_EINVAL;
-  if ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 3) return NSORT_EINVAL;
-  const Plan p = make_plan(kind, n);
+  if ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & (wide ? 7 : 3))
+    return NSORT_EINVAL;
+  const Plan p = make_plan(kind, n, wide ? dtype : 0);
   if (p.total > 0) {
     if (!tmp || tmp_bytes < p.total) return NSORT_ENOMEM;
     if (reinterpret_cast<uintptr_t>(tmp) & 255) return NSORT_EINVAL;
@@ -989,6 +1187,10 @@ extern "C" int nsort_keys(const void *d_keys_in, void *d_keys_out, uint64_t n, i
   const int rc = check_common(d_keys_in, d_keys_out, n, dtype, d_tmp, tmp_bytes,
                               NSORT_KIND_KEYS);
   if (rc != NSORT_OK || n == 0) return rc;
+  if (is_wide(dtype))
+    return sort_keys64_impl(static_cast<const uint64_t *>(d_keys_in),
+                            static_cast<uint64_t *>(d_keys_out), (int64_t)n, dtype, d_tmp,
+                            static_cast<cudaStream_t>(stream));
   return sort_keys_impl(static_cast<const uint32_t *>(d_keys_in),
                         static_cast<uint32_t *>(d_keys_out), (int64_t)n, dtype, d_tmp,
                         static_cast<cudaStream_t>(stream));

@@ -29,10 +29,13 @@ struct Plan {
   size_t total = 0;          // bytes of scratch (0 when one tile holds everything)
 };
 
-Plan make_plan(int kind, uint64_t n);
+// dtype matters only for keys: 64-bit dtypes take 8-byte words.
+Plan make_plan(int kind, uint64_t n, int dtype = 0);
 
 int sort_keys_impl(const uint32_t *in, uint32_t *out, int64_t n, int dt, void *tmp,
                    cudaStream_t st);
+int sort_keys64_impl(const uint64_t *in, uint64_t *out, int64_t n, int dt, void *tmp,
+                     cudaStream_t st);
 int sort_pairs_impl(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
                     int64_t n, int dt, void *tmp, cudaStream_t st);
 
@@ -41,7 +44,7 @@ size_t segmented_temp_bytes(int kind, uint64_t n, uint64_t nseg);
 // Kernel ids of the tracer (order of its name table).
 enum TraceKernel {
   TK_TILE_SORT_KEYS = 0, TK_TILE_SORT_PAIRS, TK_PARTITION, TK_MERGE_KEYS, TK_MERGE_PAIRS,
-  TK_SEG_BIN, TK_SEG_SORT, TK_SEG_MERGE, TK_SEG_COPY
+  TK_SEG_BIN, TK_SEG_SORT, TK_SEG_MERGE, TK_SEG_COPY, TK_TILE_SORT_KEYS64, TK_MERGE_KEYS64
 };
 
 // Brackets one kernel launch with CUDA events on its stream while tracing

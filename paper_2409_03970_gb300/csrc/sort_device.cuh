@@ -25,7 +25,7 @@
 
 namespace nsort {
 
-enum { DT_U32 = 0, DT_I32 = 1, DT_F32 = 2 };
+enum { DT_U32 = 0, DT_I32 = 1, DT_F32 = 2, DT_U64 = 3, DT_I64 = 4, DT_F64 = 5 };
 
 // Order-preserving map of a 32-bit pattern to an unsigned key.
 //  u32: identity.  i32: flip the sign bit.  f32: negatives (sign set) are
@@ -42,6 +42,21 @@ __device__ __forceinline__ uint32_t from_key(uint32_t k, int dt) {
   uint32_t m = 0u;
   if (dt == DT_I32) m = 0x80000000u;
   if (dt == DT_F32) m = (uint32_t)((int32_t)~k >> 31) | 0x80000000u;
+  return k ^ m;
+}
+
+// The same maps on 64-bit patterns (u64, i64, binary64 totalOrder).
+__device__ __forceinline__ uint64_t to_key(uint64_t b, int dt) {
+  uint64_t m = 0ull;
+  if (dt == DT_I64) m = 0x8000000000000000ull;
+  if (dt == DT_F64) m = (uint64_t)((int64_t)b >> 63) | 0x8000000000000000ull;
+  return b ^ m;
+}
+
+__device__ __forceinline__ uint64_t from_key(uint64_t k, int dt) {
+  uint64_t m = 0ull;
+  if (dt == DT_I64) m = 0x8000000000000000ull;
+  if (dt == DT_F64) m = (uint64_t)((int64_t)~k >> 63) | 0x8000000000000000ull;
   return k ^ m;
 }
 
@@ -190,8 +205,8 @@ __device__ __forceinline__ int merge_path_smem(const K *s, int a0, int na, int b
 }
 
 // Same search on global memory, one thread (64-bit lengths).
-__device__ __forceinline__ int64_t merge_path_global(const uint32_t *A, int64_t na,
-                                                     const uint32_t *B, int64_t nb,
+template <typename K>
+__device__ __forceinline__ int64_t merge_path_global(const K *A, int64_t na, const K *B, int64_t nb,
                                                      int64_t diag) {
   int64_t lo = diag - nb > 0 ? diag - nb : 0;
   int64_t hi = diag < na ? diag : na;
@@ -240,7 +255,8 @@ __device__ __forceinline__ int64_t merge_path_global_warp(const uint32_t *A, int
 
 // Merge path on unpadded shared memory: A and B are separate contiguous
 // runs (the merge pass stages them with bulk copies, which cannot pad).
-__device__ __forceinline__ int merge_path_plain(const uint32_t *s, int a0, int na, int b0, int nb,
+template <typename K>
+__device__ __forceinline__ int merge_path_plain(const K *s, int a0, int na, int b0, int nb,
                                                 int diag) {
   int lo = diag - nb > 0 ? diag - nb : 0;
   int hi = diag < na ? diag : na;
@@ -256,19 +272,19 @@ __device__ __forceinline__ int merge_path_plain(const uint32_t *s, int a0, int n
 // stable merge of s[a, a_end) and s[b, b_end) (A first on ties).  Reads at
 // most VT + 1 elements past the larger end.  With TRACK, src[k] receives
 // the index in s that output k came from.
-template <int VT, bool TRACK = false>
-__device__ __forceinline__ void serial_merge_plain(const uint32_t *s, int a, int a_end, int b,
-                                                   int b_end, uint32_t (&out)[VT],
+template <int VT, bool TRACK = false, typename K = uint32_t>
+__device__ __forceinline__ void serial_merge_plain(const K *s, int a, int a_end, int b,
+                                                   int b_end, K (&out)[VT],
                                                    int (&src)[VT]) {
-  uint32_t ka = s[a];
-  uint32_t kb = s[b];
+  K ka = s[a];
+  K kb = s[b];
 #pragma unroll
   for (int k = 0; k < VT; ++k) {
     const bool take_a = (b >= b_end) || (a < a_end && ka <= kb);
     out[k] = take_a ? ka : kb;
     if (TRACK) src[k] = take_a ? a : b;
     const int nx = (take_a ? a : b) + 1;
-    const uint32_t kn = s[nx];
+    const K kn = s[nx];
     a = take_a ? nx : a;
     b = take_a ? b : nx;
     ka = take_a ? kn : ka;
@@ -277,21 +293,20 @@ __device__ __forceinline__ void serial_merge_plain(const uint32_t *s, int a, int
 }
 
 // Keys-only serial merge without bounds checks: both runs must be followed
-// in shared memory by at least VT copies of the largest key (0xFFFFFFFF).
+// in shared memory by at least VT copies of the largest key (all ones).
 // Once a run is exhausted its head reads as the largest key, so the other
 // run is taken; when both heads are the largest key, either may be output —
 // keys only, so equal keys are the same bits and the outputs are exact.
-template <int VT>
-__device__ __forceinline__ void serial_merge_sentinel(const uint32_t *s, int a, int b,
-                                                      uint32_t (&out)[VT]) {
-  uint32_t ka = s[a];
-  uint32_t kb = s[b];
+template <int VT, typename K>
+__device__ __forceinline__ void serial_merge_sentinel(const K *s, int a, int b, K (&out)[VT]) {
+  K ka = s[a];
+  K kb = s[b];
 #pragma unroll
   for (int k = 0; k < VT; ++k) {
     const bool take_a = ka <= kb;
     out[k] = take_a ? ka : kb;
     const int nx = (take_a ? a : b) + 1;
-    const uint32_t kn = s[nx];
+    const K kn = s[nx];
     a = take_a ? nx : a;
     b = take_a ? b : nx;
     ka = take_a ? kn : ka;

@@ -127,4 +127,11 @@ __device__ __forceinline__ void store_keep_in_l2(uint32_t *p, uint32_t v) {
                : "memory");
 }
 
+__device__ __forceinline__ void store_keep_in_l2(uint64_t *p, uint64_t v) {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  asm volatile("st.global.L2::cache_hint.b64 [%0], %1, %2;" ::"l"(p), "l"(v), "l"(pol)
+               : "memory");
+}
+
 }  // namespace nsort

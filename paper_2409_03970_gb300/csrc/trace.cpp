@@ -16,7 +16,8 @@ namespace {
 
 const char *const kKernelNames[] = {"tile_sort_keys", "tile_sort_pairs", "partition",
                                     "merge_keys",     "merge_pairs",     "segmented_bin",
-                                    "segmented_sort", "segmented_merge", "segmented_copy"};
+                                    "segmented_sort", "segmented_merge", "segmented_copy",
+                                    "tile_sort_keys64", "merge_keys64"};
 constexpr int kNumKernels = sizeof(kKernelNames) / sizeof(kKernelNames[0]);
 
 struct Rec {

@@ -19,6 +19,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libnsort.so")
 
 U32, I32, F32 = 0, 1, 2
+U64, I64, F64 = 3, 4, 5           # 64-bit keys (nsort_keys only)
 KIND_KEYS, KIND_PAIRS, KIND_SEGMENTED, KIND_SEGMENTED_PAIRS = 0, 1, 2, 3
 OK, EINVAL, ENOMEM, ECUDA, EBUSY, ETIMEOUT, ENOTFOUND = range(7)
 NET_BITONIC, NET_ODDEVEN, NET_BEST = 0, 1, 2     # include/nsort_ablation.h
@@ -78,6 +79,8 @@ def _load():
         lib.nsort_temp_bytes.restype = sz
         lib.nsort_plan.argtypes = [i32, u64, ip, ip, ip]
         lib.nsort_plan.restype = i32
+        lib.nsort_plan_dtype.argtypes = [i32, u64, i32, ip, ip, ip]
+        lib.nsort_plan_dtype.restype = i32
         lib.nsort_keys.argtypes = [vp, vp, u64, i32, vp, sz, vp]
         lib.nsort_keys.restype = i32
         lib.nsort_pairs.argtypes = [vp, vp, vp, vp, u64, i32, vp, sz, vp]
@@ -156,13 +159,16 @@ def _stream(stream) -> int:
 
 
 def dtype_code(t) -> int:
-    """nsort_dtype of a torch tensor (uint32 / int32 / float32)."""
+    """nsort_dtype of a torch tensor (uint32 / int32 / float32, or the 64-bit
+    uint64 / int64 / float64)."""
     import torch
-    codes = {torch.int32: I32, torch.float32: F32}
+    codes = {torch.int32: I32, torch.float32: F32, torch.int64: I64, torch.float64: F64}
     if hasattr(torch, "uint32"):
         codes[torch.uint32] = U32
+    if hasattr(torch, "uint64"):
+        codes[torch.uint64] = U64
     if t.dtype not in codes:
-        raise TypeError(f"keys must be uint32, int32 or float32, not {t.dtype}")
+        raise TypeError(f"keys must be (u)int32, float32, (u)int64 or float64, not {t.dtype}")
     return codes[t.dtype]
 
 
@@ -177,12 +183,13 @@ def nsort_temp_bytes(kind: int, n: int, nseg: int = 0, dtype: int = U32) -> int:
     return int(_load().nsort_temp_bytes(kind, n, nseg, dtype))
 
 
-def nsort_plan(kind: int, n: int):
-    """(passes, sort_tile, merge_tile) of a plain sort of n keys."""
+def nsort_plan(kind: int, n: int, dtype: int = U32):
+    """(passes, sort_tile, merge_tile) of a plain sort of n keys of dtype."""
     p, s, m = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-    rc = _load().nsort_plan(kind, n, ctypes.byref(p), ctypes.byref(s), ctypes.byref(m))
+    rc = _load().nsort_plan_dtype(kind, n, dtype, ctypes.byref(p), ctypes.byref(s),
+                                  ctypes.byref(m))
     if rc != OK:
-        raise NsortError(rc, "nsort_plan")
+        raise NsortError(rc, "nsort_plan_dtype")
     return p.value, s.value, m.value
 
 
@@ -404,17 +411,18 @@ def nsort_trace_read() -> dict:
 
 # ---- conveniences -----------------------------------------------------------
 
-def scratch(kind: int, n: int, nseg: int = 0, device=None):
-    """A uint8 device tensor of nsort_temp_bytes(kind, n, nseg) bytes (at
-    least one byte, so that it has an address)."""
+def scratch(kind: int, n: int, nseg: int = 0, device=None, dtype: int = U32):
+    """A uint8 device tensor of nsort_temp_bytes(kind, n, nseg, dtype) bytes
+    (at least one byte, so that it has an address)."""
     import torch
-    nbytes = max(1, nsort_temp_bytes(kind, n, nseg))
+    nbytes = max(1, nsort_temp_bytes(kind, n, nseg, dtype))
     return torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
 
 
 def sort(keys, out=None, tmp=None, stream=None):
-    """Sorts a 1-D CUDA tensor of uint32 / int32 / float32 keys ascending
-    (float32 in IEEE totalOrder).  Returns `out` (new tensor if None)."""
+    """Sorts a 1-D CUDA tensor of uint32 / int32 / float32 (or 64-bit) keys
+    ascending (floats in IEEE totalOrder).  Returns `out` (new tensor if
+    None)."""
     import torch
     _check_1d(keys, "keys")
     dt = dtype_code(keys)
@@ -423,7 +431,7 @@ def sort(keys, out=None, tmp=None, stream=None):
         out = torch.empty_like(keys)
     _check_1d(out, "out")
     if tmp is None:
-        tmp = scratch(KIND_KEYS, n, device=keys.device)
+        tmp = scratch(KIND_KEYS, n, device=keys.device, dtype=dt)
     rc = nsort_keys(keys, out, n, dt, tmp, tmp.numel(), stream)
     if rc != OK:
         raise NsortError(rc, "nsort_keys")

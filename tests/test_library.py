@@ -158,3 +158,23 @@ def test_merge_runs_argument_validation_needs_no_gpu(lib):
     assert nsort.merge_run_lengths(H, 16) == [16, 32, 64, 128, 256]
     assert nsort.merge_run_lengths(S, 4) == [1, 2, 4, 8, 16, 32, 64]
     assert nsort.merge_run_lengths(R, 4)[0] == 2 and nsort.merge_run_lengths(R, 4)[-1] == 1024
+
+
+def test_64bit_keys_plan_scratch_and_validation(lib):
+    p, st, mt = nsort.nsort_plan(nsort.KIND_KEYS, 1 << 27, nsort.U64)
+    assert (st, mt) == (4096, 1920) and p == 1 + (27 - 12)
+    assert nsort.nsort_plan(nsort.KIND_KEYS, 4096, nsort.F64)[0] == 1
+    assert nsort.nsort_plan(nsort.KIND_KEYS, 4097, nsort.I64)[0] == 2
+    n = 1 << 20
+    t64 = nsort.nsort_temp_bytes(nsort.KIND_KEYS, n, 0, nsort.U64)
+    assert 8 * n <= t64 <= 8 * n + 8 * (n // 1920 + n // 8192 + 3) + 8 * (n // 64 + 2) + 1280
+    assert nsort.nsort_temp_bytes(nsort.KIND_KEYS, 4096, 0, nsort.U64) == 0    # one tile
+    # 64-bit keys: nsort_keys only, 8-byte aligned pointers
+    assert nsort.nsort_keys(0x1004, 0x2000, 1 << 20, nsort.U64, 0x100000, t64, 0) == nsort.EINVAL
+    assert nsort.nsort_keys(0x1000, 0x2000, 1 << 20, nsort.F64, 0x100000, t64 - 8, 0) == nsort.ENOMEM
+    assert nsort.nsort_pairs(0x1000, 0x3000, 0x2000, 0x4000, 10, nsort.U64, 0, 0, 0) == nsort.EINVAL
+    assert nsort.nsort_segmented(0x1000, 0x2000, 0, 0, 0x3000, 1, 10, nsort.I64, 0x4000, 1 << 20,
+                                 0) == nsort.EINVAL
+    assert nsort.nsort_keys(0x1000, 0x2000, 10, 6, 0, 0, 0) == nsort.EINVAL
+    with pytest.raises(nsort.NsortError):
+        nsort.nsort_plan(nsort.KIND_PAIRS, 100, nsort.U64)
