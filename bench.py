@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["nsort", "reference"], default="nsort")
     ap.add_argument("--log2n", type=int, default=28)
-    ap.add_argument("--dtype", choices=["u32", "i32", "f32"], default="u32")
+    ap.add_argument("--dtype", choices=["u32", "i32", "f32", "u64", "i64", "f64"], default="u32")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
@@ -186,12 +186,29 @@ def load_traffic(kernel: str):
 
 # ---- CPU oracle timing ---------------------------------------------------------
 
+WIDE = ("u64", "i64", "f64")
+
+
+def sample_keys(n: int, dtype: str, seed: int = 0) -> np.ndarray:
+    """Uniform keys of the plain workload: uint32 patterns, or uint64 ones
+    for the 64-bit dtypes."""
+    from paper_2409_03970_gb300 import inputs
+    if dtype in WIDE:
+        return inputs.keys64(n, dtype, "uniform", seed=seed)
+    return inputs.keys(n, dtype, "uniform", seed=seed)
+
+
+def oracle_sort(bits: np.ndarray, dtype: str):
+    import oracle
+    return oracle.sort_keys64(bits, dtype) if dtype in WIDE else oracle.sort_keys(bits, dtype)
+
+
 def time_oracle(bits: np.ndarray, dtype: str, seconds: float):
     import oracle
     oracle.build()
     reps, t0 = 0, time.perf_counter()
     while True:
-        oracle.sort_keys(bits, dtype)
+        oracle_sort(bits, dtype)
         reps += 1
         el = time.perf_counter() - t0
         if el >= seconds:
@@ -202,7 +219,7 @@ def time_oracle(bits: np.ndarray, dtype: str, seconds: float):
 def cpu_baseline(dtype: str):
     from paper_2409_03970_gb300 import inputs
     n = 1 << CPU_BASELINE_LOG2
-    x = inputs.keys(n, dtype, "uniform", seed=0)
+    x = sample_keys(n, dtype)
     reps, el = time_oracle(x, dtype, CPU_BASELINE_SECONDS)
     return {"value": reps * n / el / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"first 2^{CPU_BASELINE_LOG2} keys of the workload (uniform {dtype}, "
@@ -213,16 +230,15 @@ def cpu_baseline(dtype: str):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    from paper_2409_03970_gb300 import inputs
     n = 1 << REFERENCE_SAMPLE_LOG2
-    x = inputs.keys(n, args.dtype, "uniform", seed=0)
+    x = sample_keys(n, args.dtype)
     import oracle
     oracle.build()
     for _ in range(args.warmup):
-        oracle.sort_keys(x, args.dtype)
+        oracle_sort(x, args.dtype)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.sort_keys(x, args.dtype)
+        oracle_sort(x, args.dtype)
     el = time.perf_counter() - t0
     ms = el * 1e3 / args.steps
     value = n / (ms / 1e3) / 1e9
@@ -243,7 +259,7 @@ def run_reference(args, rank, world):
     }), flush=True)
 
 
-def bench_e2e(nsort, torch, host_in, x, out, tmp, n, code, steps, world):
+def bench_e2e(nsort, torch, host_in, x, out, tmp, n, code, steps, world, esize=4):
     """The same sort through the public API with HOST buffers: every step
     copies its input from pinned host memory, sorts, and copies the result
     back to pinned host memory.  Pipelined over three streams with double
@@ -302,7 +318,7 @@ def bench_e2e(nsort, torch, host_in, x, out, tmp, n, code, steps, world):
     torch.cuda.synchronize()
     serial_ms = s0.elapsed_time(s1)
     return {"value": world * n / (ems / 1e3) / 1e9, "unit": UNIT,
-            "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 4 * n, "ms_per_step": ems,
+            "h2d_bytes_per_step": esize * n, "d2h_bytes_per_step": esize * n, "ms_per_step": ems,
             "steps": ke, "pipelined": "3 streams, double-buffered device arrays",
             "one_step_unpipelined_ms": serial_ms}
 
@@ -697,14 +713,18 @@ def main():
         return
 
     n = 1 << args.log2n
-    code = {"u32": nsort.U32, "i32": nsort.I32, "f32": nsort.F32}[args.dtype]
-    bits = inputs.keys(n, args.dtype, "uniform", seed=rank)
-    host_in = torch.from_numpy(bits.view(np.int32)).pin_memory()
+    code = {"u32": nsort.U32, "i32": nsort.I32, "f32": nsort.F32,
+            "u64": nsort.U64, "i64": nsort.I64, "f64": nsort.F64}[args.dtype]
+    wide = args.dtype in WIDE
+    esize = 8 if wide else 4                              # bytes per key
+    bits = sample_keys(n, args.dtype, seed=rank)
+    host_in = torch.from_numpy(bits.view(np.int64 if wide else np.int32)).pin_memory()
     del bits
     x = host_in.cuda()
     out = torch.empty_like(x)
-    tmp = nsort.scratch(nsort.KIND_KEYS, n)
-    passes, sort_tile, merge_tile = nsort.nsort_plan(nsort.KIND_KEYS, n)
+    tmp = nsort.scratch(nsort.KIND_KEYS, n, dtype=code)
+    passes, sort_tile, merge_tile = nsort.nsort_plan(nsort.KIND_KEYS, n, code)
+    mk_name = "merge_keys64" if wide else "merge_keys"
     stream = torch.cuda.current_stream()
     sh = stream.cuda_stream
 
@@ -742,25 +762,25 @@ def main():
     value = world * n / (ms / 1e3) / 1e9
 
     peaks = load_peaks()
-    alg_bytes_sort = passes * 8 * n                      # every pass reads and writes 4 B/key
+    alg_bytes_sort = passes * 2 * esize * n              # every pass reads and writes each key
     sort_frac = alg_bytes_sort / (ms / 1e3) / 1e9 / peaks["hbm_gbs"]
-    mk = trace.get("merge_keys")
+    mk = trace.get(mk_name)
     roofline = None
     if mk:
         per_launch_ms = mk["total_ms"] / mk["launches"]
-        achieved = 8 * n / (per_launch_ms / 1e3) / 1e9
-        tr = load_traffic("merge_keys")
-        roofline = {"bound": "hbm", "kernel": "merge_keys", "achieved": achieved,
+        achieved = 2 * esize * n / (per_launch_ms / 1e3) / 1e9
+        tr = load_traffic(mk_name)
+        roofline = {"bound": "hbm", "kernel": mk_name, "achieved": achieved,
                     "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
                     "peak_source": peaks["source"],
                     "traffic": (tr["bytes_per_key"] * n) if tr else None,
-                    "algorithmic_bytes": 8 * n, "launch_ms": per_launch_ms,
+                    "algorithmic_bytes": 2 * esize * n, "launch_ms": per_launch_ms,
                     "share_of_step": mk["total_ms"] / (ms * args.steps)}
     launches = sum(v["launches"] for v in trace.values()) // args.steps
 
     e2e = None
     if not args.no_e2e:
-        e2e = bench_e2e(nsort, torch, host_in, x, out, tmp, n, code, args.steps, world)
+        e2e = bench_e2e(nsort, torch, host_in, x, out, tmp, n, code, args.steps, world, esize)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -786,7 +806,9 @@ def main():
             "config": {"workload": f"plain sort, 2^{args.log2n} {args.dtype} keys, uniform, "
                                    f"seed = rank; replicas (one array per GPU)",
                        "n": n, "passes": passes, "sort_tile": sort_tile, "merge_tile": merge_tile,
-                       "l2": "inputs (1 GiB) larger than L2; no flush",
+                       "l2": (f"inputs ({esize * n / 2**30:.2f} GiB) larger than L2; no flush"
+                              if esize * n > (256 << 20) else
+                              "inputs not larger than L2: a small-case run, not a bench value"),
                        "sort_hbm_roofline_frac": sort_frac,
                        "sort_algorithmic_bytes": alg_bytes_sort,
                        "parallelism": f"replicas x{world}"},
