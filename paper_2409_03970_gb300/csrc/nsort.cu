@@ -80,21 +80,29 @@ __device__ __forceinline__ bool aligned16(const void *p) {
 // samples first (section "sampled partition" below).
 constexpr int SAMPLE = 64;
 
-template <int NT, int DT, bool FINAL>
+// Column sort of the keys tile sort: the fewest-comparator network of the
+// thread's width (Table 1): Green's 60 comparators for 16 keys, two of them
+// and an odd-even merge (185) for 32.
+struct BestColumns {
+  template <typename K, int W>
+  __device__ __forceinline__ static void sort(K (&r)[W]) { column_sort_net<NET_BEST, W>(r); }
+};
+
+template <int NT, int IPT, int DT, bool FINAL>
 __global__ void __launch_bounds__(NT) tile_sort_keys_kernel(const uint32_t *in, uint32_t *out,
                                                             int64_t n, uint32_t *samp) {
-  constexpr int TILE = NT * 16;
-  extern __shared__ __align__(16) unsigned char tile_smem[];   // merge_smem_len(TILE, 16) words
+  constexpr int TILE = NT * IPT;
+  extern __shared__ __align__(16) unsigned char tile_smem[];   // merge_smem_len(TILE, IPT) words
   uint32_t *s = reinterpret_cast<uint32_t *>(tile_smem);
   const int tid = threadIdx.x;
   const int64_t base = (int64_t)blockIdx.x * TILE;
   const int count = (int)(n - base < TILE ? n - base : TILE);
   const bool full = count == TILE && aligned16(in + base) && aligned16(out + base);
-  uint32_t r[16];
+  uint32_t r[IPT];
   if (full) {
     const uint4 *p = reinterpret_cast<const uint4 *>(in + base);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < IPT / 4; ++j) {
       const uint4 v = p[tid + NT * j];
       r[4 * j + 0] = to_key(v.x, DT);
       r[4 * j + 1] = to_key(v.y, DT);
@@ -103,7 +111,7 @@ __global__ void __launch_bounds__(NT) tile_sort_keys_kernel(const uint32_t *in, 
     }
   } else {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < IPT / 4; ++j) {
 #pragma unroll
       for (int w = 0; w < 4; ++w) {
         const int e = 4 * (tid + NT * j) + w;
@@ -111,11 +119,11 @@ __global__ void __launch_bounds__(NT) tile_sort_keys_kernel(const uint32_t *in, 
       }
     }
   }
-  sort_tile_in_block<NT, 16, Green16Columns>(r, s);
-  store_run<16, FINAL ? DT : DT_U32>(r, out + base, count, full);
-  static_assert(SAMPLE % 16 == 0, "a sample starts a thread's run of 16");
-  if (!FINAL && samp && !(tid & (SAMPLE / 16 - 1)) && tid * 16 < count)
-    store_keep_in_l2(samp + (base + tid * 16) / SAMPLE, r[0]);
+  sort_tile_in_block<NT, IPT, BestColumns>(r, s);
+  store_run<IPT, FINAL ? DT : DT_U32>(r, out + base, count, full);
+  static_assert(SAMPLE % IPT == 0, "a sample starts a thread's run");
+  if (!FINAL && samp && !(tid & (SAMPLE / IPT - 1)) && tid * IPT < count)
+    store_keep_in_l2(samp + (base + tid * IPT) / SAMPLE, r[0]);
 }
 
 // Tile sort, key/value pairs.  The networks sort 64-bit composites
@@ -674,7 +682,8 @@ __global__ void __launch_bounds__(NT, PAIRS ? 3 : 4) merge_tma_kernel(
 
 namespace {
 
-constexpr int KEYS_SORT_NT = 512;   // tile sort: 512 threads x 16 keys = 8192
+constexpr int KEYS_SORT_NT = 512;   // tile sort: 512 threads x 32 keys = 16384
+constexpr int KEYS_SORT_IPT = 32;
 constexpr int PAIRS_SORT_NT = 256;  //            256 threads x 16 pairs = 4096
 constexpr int MERGE_NT = 256;       // merge pass: 256 threads x 16 = 4096 outputs
 constexpr int MERGE_VT = 16;
@@ -711,8 +720,9 @@ constexpr size_t KEYS64_SORT_SMEM =
     sizeof(uint64_t) * merge_smem_len<uint64_t>(KEYS64_SORT_TILE, 16);
 constexpr int MERGE64_TILE = MERGE64_NT * MERGE64_VT;
 
-constexpr int KEYS_SORT_TILE = KEYS_SORT_NT * 16;
-constexpr size_t KEYS_SORT_SMEM = sizeof(uint32_t) * merge_smem_len<uint32_t>(KEYS_SORT_TILE, 16);
+constexpr int KEYS_SORT_TILE = KEYS_SORT_NT * KEYS_SORT_IPT;
+constexpr size_t KEYS_SORT_SMEM =
+    sizeof(uint32_t) * merge_smem_len<uint32_t>(KEYS_SORT_TILE, KEYS_SORT_IPT);
 constexpr int PAIRS_SORT_TILE = PAIRS_SORT_NT * 16;
 constexpr int MERGE_TILE = MERGE_NT * MERGE_VT;
 constexpr int PMERGE_TILE = PMERGE_NT * PMERGE_VT;
@@ -774,7 +784,7 @@ static int launch_status(const char *what) {
 
 template <int DT, bool FIN>
 static void keys_sort_smem_attr() {
-  cudaFuncSetAttribute(tile_sort_keys_kernel<KEYS_SORT_NT, DT, FIN>,
+  cudaFuncSetAttribute(tile_sort_keys_kernel<KEYS_SORT_NT, KEYS_SORT_IPT, DT, FIN>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)KEYS_SORT_SMEM);
 }
 
@@ -794,7 +804,8 @@ static void launch_tile_sort_keys(const uint32_t *in, uint32_t *out, int64_t n, 
     done_mask.fetch_or(bit);
   }
 #define NSORT_TSK(DT, FIN)                                                        \
-  tile_sort_keys_kernel<KEYS_SORT_NT, DT, FIN><<<grid, KEYS_SORT_NT, KEYS_SORT_SMEM, st>>>( \
+  tile_sort_keys_kernel<KEYS_SORT_NT, KEYS_SORT_IPT, DT, FIN>                             \
+      <<<grid, KEYS_SORT_NT, KEYS_SORT_SMEM, st>>>(                                       \
       in, out, n, samp)
   if (dt == DT_U32) { if (final_pass) NSORT_TSK(DT_U32, true); else NSORT_TSK(DT_U32, false); }
   else if (dt == DT_I32) { if (final_pass) NSORT_TSK(DT_I32, true); else NSORT_TSK(DT_I32, false); }
