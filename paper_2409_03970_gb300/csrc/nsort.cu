@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(NT) tile_sort_keys_kernel(const uint32_t *in, 
 // so the network's result is the stable order.  Values are staged in shared
 // memory and gathered by position at the end.
 template <int NT, int DT, bool FINAL>
-__global__ void __launch_bounds__(NT) tile_sort_pairs_kernel(const uint32_t *kin,
+__global__ void __launch_bounds__(NT, 2) tile_sort_pairs_kernel(const uint32_t *kin,
                                                              const uint32_t *vin,
                                                              uint32_t *kout, uint32_t *vout,
                                                              int64_t n, uint32_t *samp) {
@@ -684,7 +684,7 @@ namespace {
 
 constexpr int KEYS_SORT_NT = 512;   // tile sort: 512 threads x 32 keys = 16384
 constexpr int KEYS_SORT_IPT = 32;
-constexpr int PAIRS_SORT_NT = 256;  //            256 threads x 16 pairs = 4096
+constexpr int PAIRS_SORT_NT = 512;  //            512 threads x 16 pairs = 8192
 constexpr int MERGE_NT = 256;       // merge pass: 256 threads x 16 = 4096 outputs
 constexpr int MERGE_VT = 16;
 constexpr int PMERGE_NT = 256;
