@@ -259,6 +259,56 @@ def run_reference(args, rank, world):
     }), flush=True)
 
 
+def bind_to_gpu_numa_node(torch, dev: int):
+    """Restricts this process to the CPUs of the GPU's NUMA node (when sysfs
+    names one and it overlaps the allowed CPUs), so that pinned host buffers
+    allocated afterwards sit next to the GPU.  Returns the node or None."""
+    try:
+        pr = torch.cuda.get_device_properties(dev)
+        bdf = f"{pr.pci_domain_id:04x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0"
+        node = int(open(f"/sys/bus/pci/devices/{bdf}/numa_node").read().strip())
+        if node < 0:
+            return None
+        cpus = set()
+        for part in open(f"/sys/devices/system/node/node{node}/cpulist").read().strip().split(","):
+            lo, _, hi = part.partition("-")
+            cpus.update(range(int(lo), int(hi or lo) + 1))
+        allowed = cpus & os.sched_getaffinity(0)
+        if not allowed:
+            return None
+        os.sched_setaffinity(0, allowed)
+        return node
+    except (OSError, ValueError, AttributeError):
+        return None
+
+
+def copy_bandwidths(torch, host, dev_a, dev_b):
+    """GB/s of one host-to-device copy of `host` (pinned) into dev_a alone,
+    one device-to-host copy of dev_b alone, and of both at once on two
+    streams."""
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    back = torch.empty_like(host).pin_memory()
+    nbytes = host.numel() * host.element_size()
+    res = {}
+    for name in ("h2d", "d2h", "both"):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(s1)
+        s2.wait_event(a)
+        if name in ("h2d", "both"):
+            with torch.cuda.stream(s1):
+                dev_a.copy_(host, non_blocking=True)
+        if name in ("d2h", "both"):
+            with torch.cuda.stream(s2):
+                back.copy_(dev_b, non_blocking=True)
+        s1.wait_stream(s2)
+        b.record(s1)
+        torch.cuda.synchronize()
+        res[name + "_gbs"] = (2 if name == "both" else 1) * nbytes / (a.elapsed_time(b) / 1e3) / 1e9
+    return res
+
+
 def bench_e2e(nsort, torch, host_in, x, out, tmp, n, code, steps, world, esize=4):
     """The same sort through the public API with HOST buffers: every step
     copies its input from pinned host memory, sorts, and copies the result
@@ -317,7 +367,8 @@ def bench_e2e(nsort, torch, host_in, x, out, tmp, n, code, steps, world, esize=4
     s1.record(comp)
     torch.cuda.synchronize()
     serial_ms = s0.elapsed_time(s1)
-    return {"value": world * n / (ems / 1e3) / 1e9, "unit": UNIT,
+    bw = copy_bandwidths(torch, host_in, din[1], dout[1])
+    return {"value": world * n / (ems / 1e3) / 1e9, "unit": UNIT, "copy_bandwidths": bw,
             "h2d_bytes_per_step": esize * n, "d2h_bytes_per_step": esize * n, "ms_per_step": ems,
             "steps": ke, "pipelined": "3 streams, double-buffered device arrays",
             "one_step_unpipelined_ms": serial_ms}
@@ -683,6 +734,7 @@ def main():
     from paper_2409_03970_gb300 import inputs, nsort
 
     torch.cuda.set_device(local_rank)
+    numa_node = bind_to_gpu_numa_node(torch, local_rank)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
@@ -781,6 +833,7 @@ def main():
     e2e = None
     if not args.no_e2e:
         e2e = bench_e2e(nsort, torch, host_in, x, out, tmp, n, code, args.steps, world, esize)
+        e2e["host_numa_node"] = numa_node
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
