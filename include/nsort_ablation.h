@@ -3,9 +3,10 @@
  * of keys per thread of the block sort, varied one at a time, so that the
  * paper's Table 1 (comparators per network) and Table 2 (time to produce
  * sorted runs of X elements with R registers) can be measured on the GPU.
- * The production sorts (nsort.h) use the best 16-input network with 16 keys
- * per thread; these calls run the same column sort, warp merge and block
- * merge code with another network or another keys-per-thread count.
+ * The production sorts (nsort.h) use the best networks with 32 keys per
+ * thread for 32-bit keys (16 for pairs and 64-bit keys); these calls run
+ * the same column sort, warp merge and block merge code with another
+ * network or another keys-per-thread count.
  *
  * Keys are unsigned 32-bit integers (the paper's 32-bit integer keys,
  * Sec. 2.2), ascending.  Device pointers are caller-owned CUDA device

@@ -2,14 +2,16 @@
 //
 // The paper's three merge levels (Sec. 2.1, Fig. 1) become thread / warp /
 // block / grid levels here:
-//   column sort   (Sec. 2.3)  16 keys in one thread's registers, sorted by the
-//                             60-comparator 16-input network;
-//   row merge     (Sec. 2.4)  the 32 sorted 16-runs of a warp are merged by
+//   column sort   (Sec. 2.3)  16 or 32 keys in one thread's registers; each
+//                             16-key column is sorted by the 60-comparator
+//                             16-input network (two columns are then merged
+//                             in registers: 185 comparators for 32 keys);
+//   row merge     (Sec. 2.4)  the 32 sorted runs of a warp are merged by
 //                             flip ("asymmetric") bitonic merging networks:
 //                             stages whose comparators span lanes use warp
-//                             shuffles (the vectorised part), the last four
-//                             stages run inside each thread (the serial tail
-//                             of the hybrid merger);
+//                             shuffles (the vectorised part), the stages
+//                             inside a thread's run run in registers (the
+//                             serial tail of the hybrid merger);
 //   vectorised / parallel merge (Sec. 2.1, last paragraph) merge path: each
 //                             thread finds its share of a merge by a binary
 //                             search on the cross diagonal and runs a
