@@ -445,9 +445,10 @@ def bench_keys64(nsort, torch):
                      ("f64", "specials")):
         x = torch.from_numpy(inputs.keys64(m, dt, dist, seed=0).view(np.int64)).cuda()
         code = codes[dt]
-        nsort.nsort_trace_enable(True)
-        ms = time_sort(nsort, torch,
-                       lambda: nsort.nsort_keys(x, ko, m, code, tmp, tmp.numel()))
+        fn = lambda: nsort.nsort_keys(x, ko, m, code, tmp, tmp.numel())
+        ms = time_sort(nsort, torch, fn)
+        nsort.nsort_trace_enable(True)            # launch durations from a traced repeat
+        time_sort(nsort, torch, fn, reps=3, warm=0)
         tr = nsort.nsort_trace_read()
         nsort.nsort_trace_enable(False)
         r = {"ms": ms, "gkeys_s": m / ms / 1e6, "passes": passes,
@@ -796,7 +797,6 @@ def main():
         pass
     clocks = ClockSampler(uuid)
     clocks.start()
-    nsort.nsort_trace_enable(True)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     barrier(world)
@@ -807,11 +807,23 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     barrier(world)
-    clk = clocks.stop()
-    trace = nsort.nsort_trace_read()
-    nsort.nsort_trace_enable(False)
     ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
     value = world * n / (ms / 1e3) / 1e9
+    # per-kernel durations: the same steps once more with the library's
+    # tracing on (CUDA events around every launch on its stream).  Tracing
+    # puts events between the kernels, which costs time and undoes the
+    # overlapped launches, so the step time above is taken without it.
+    nsort.nsort_trace_enable(True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    traced_ms = e0.elapsed_time(e1) / args.steps
+    trace = nsort.nsort_trace_read()
+    nsort.nsort_trace_enable(False)
 
     peaks = load_peaks()
     alg_bytes_sort = passes * 2 * esize * n              # every pass reads and writes each key
@@ -827,7 +839,9 @@ def main():
                     "peak_source": peaks["source"],
                     "traffic": (tr["bytes_per_key"] * n) if tr else None,
                     "algorithmic_bytes": 2 * esize * n, "launch_ms": per_launch_ms,
-                    "share_of_step": mk["total_ms"] / (ms * args.steps)}
+                    "share_of_step": mk["total_ms"] / (traced_ms * args.steps),
+                    "timing": "launch durations from a traced repeat of the timed steps "
+                              f"({traced_ms:.3f} ms per traced step)"}
     launches = sum(v["launches"] for v in trace.values()) // args.steps
 
     e2e = None

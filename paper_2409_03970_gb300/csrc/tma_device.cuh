@@ -41,6 +41,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   return ok != 0;
 }
 
+// Programmatic dependent launch: blocks until the grids this one depends on
+// (the previous kernel of the stream, when this one was launched with
+// programmatic stream serialisation) have completed and their memory is
+// visible; a no-op for a plain launch.  No kernel of the library triggers its
+// dependents early: each dependent launch is released when its predecessor
+// completes, which hides the launch latency without letting the next grid's
+// CTAs take SM resources while the current grid still runs.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
