@@ -410,6 +410,16 @@ def bench_configs(nsort, torch):
         del x
     del tmp, ko
     torch.cuda.empty_cache()
+    # the small plain case: 2^20 uniform uint32 keys, seed 0 (launch-latency bound)
+    s = 1 << 20
+    x = torch.from_numpy(inputs.keys(s, "u32", "uniform", seed=0).view(np.int32)).cuda()
+    y = torch.empty_like(x)
+    tmp = nsort.scratch(nsort.KIND_KEYS, s)
+    ms = time_sort(nsort, torch, lambda: nsort.nsort_keys(x, y, s, nsort.U32, tmp, tmp.numel()),
+                   reps=51, warm=5)
+    out["keys_u32_uniform_2e20"] = {"ms": ms, "gkeys_s": s / ms / 1e6,
+                                    "l2": "inputs fit in L2 (4 MiB): not an HBM measurement"}
+    del x, y, tmp
     m = 1 << 27
     k, v = inputs.normal_pairs(m, seed=0)
     kt = torch.from_numpy(k.view(np.int32)).cuda()

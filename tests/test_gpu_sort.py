@@ -191,3 +191,70 @@ def test_full_size_pairs_against_oracle(ns):
     wk, wv = oracle.sort_pairs(k, v, "f32")
     assert np.array_equal(ko, wk)
     assert np.array_equal(vo, wv)
+
+
+# ---- dependent launches ------------------------------------------------------
+
+def test_sort_captured_in_a_cuda_graph(ns):
+    """nsort_keys and nsort_pairs captured into one CUDA graph (their
+    partition and merge kernels are dependent launches) and replayed on new
+    data give the oracle's result."""
+    n = 3 * 16384 + 11
+    x = torch.empty(n, dtype=torch.int32, device="cuda")
+    y = torch.empty_like(x)
+    kv, vv = torch.empty_like(x), torch.empty_like(x)
+    ko, vo = torch.empty_like(x), torch.empty_like(x)
+    tk = ns.scratch(ns.KIND_KEYS, n)
+    tp = ns.scratch(ns.KIND_PAIRS, n)
+    s = torch.cuda.Stream()
+    x.zero_()
+    kv.zero_()
+    vv.zero_()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):      # one-time set-up (shared-memory opt-ins) before capture
+        assert ns.nsort_keys(x, y, n, DT["f32"], tk, tk.numel(), s) == ns.OK
+        assert ns.nsort_pairs(kv, vv, ko, vo, n, DT["u32"], tp, tp.numel(), s) == ns.OK
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        assert ns.nsort_keys(x, y, n, DT["f32"], tk, tk.numel(), s) == ns.OK
+        assert ns.nsort_pairs(kv, vv, ko, vo, n, DT["u32"], tp, tp.numel(), s) == ns.OK
+    for seed in (1, 2):
+        bits = inputs.keys(n, "f32", "dup16", seed=seed)
+        kb = inputs.keys(n, "u32", "zipf", seed=seed)
+        vb = np.arange(n, dtype=np.uint32)
+        x.copy_(dev(bits))
+        kv.copy_(dev(kb))
+        vv.copy_(dev(vb))
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(host(y), oracle.sort_keys(bits, "f32"))
+        wk, wv = oracle.sort_pairs(kb, vb, "u32")
+        assert np.array_equal(host(ko), wk) and np.array_equal(host(vo), wv)
+
+
+def test_plain_launches_give_the_same_result(ns, tmp_path):
+    """NSORT_NO_PDL=1 (read once per process) selects plain launches; a
+    child process sorting that way matches the oracle."""
+    import subprocess
+    import sys
+    import textwrap
+    root = __import__("os").path.dirname(__import__("os").path.dirname(__file__))
+    code = textwrap.dedent("""
+        import sys, numpy as np, torch
+        sys.path.insert(0, %r)
+        import oracle
+        from paper_2409_03970_gb300 import inputs, nsort
+        n = (1 << 20) + 77
+        bits = inputs.keys(n, "i32", "uniform", seed=3)
+        x = torch.from_numpy(bits.view(np.int32)).cuda()
+        tmp = nsort.scratch(nsort.KIND_KEYS, n)
+        assert nsort.nsort_keys(x, x, n, nsort.I32, tmp, tmp.numel()) == nsort.OK
+        assert np.array_equal(x.cpu().numpy().view(np.uint32), oracle.sort_keys(bits, "i32"))
+        print("ok")
+    """ % root)
+    env = dict(__import__("os").environ, NSORT_NO_PDL="1")
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
