@@ -98,7 +98,7 @@ template <int FAMILY, int IPT>
 __global__ void __launch_bounds__(ABL_NT) block_runs_kernel(const uint32_t *in, uint32_t *out,
                                                             int64_t n) {
   constexpr int TILE = ABL_NT * IPT;
-  extern __shared__ __align__(16) unsigned char abl_smem[];   // merge_smem_len(TILE, IPT) words
+  extern __shared__ __align__(16) unsigned char abl_smem[];   // block_smem_len<u32>(ABL_NT, IPT) words
   uint32_t *s = reinterpret_cast<uint32_t *>(abl_smem);
   const int tid = threadIdx.x;
   const int64_t base = (int64_t)blockIdx.x * TILE;
@@ -243,7 +243,7 @@ template <int IPT>
 __global__ void __launch_bounds__(ABL_NT) serial_merge_kernel(const uint32_t *in, uint32_t *out,
                                                               int64_t n, int run) {
   constexpr int TILE = ABL_NT * IPT;
-  extern __shared__ __align__(16) unsigned char abl_smem[];   // merge_smem_len(TILE, IPT) words
+  extern __shared__ __align__(16) unsigned char abl_smem[];   // block_smem_len<u32>(ABL_NT, IPT) words
   uint32_t *s = reinterpret_cast<uint32_t *>(abl_smem);
   const int tid = threadIdx.x;
   const int64_t base = (int64_t)blockIdx.x * TILE;
@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(ABL_NT) serial_merge_kernel(const uint32_t *in
 
 template <int IPT>
 constexpr size_t block_smem_bytes() {
-  return sizeof(uint32_t) * (size_t)merge_smem_len<uint32_t>(ABL_NT * IPT, IPT);
+  return sizeof(uint32_t) * (size_t)block_smem_len<uint32_t>(ABL_NT, IPT);
 }
 
 int launch_error(const char *what) {

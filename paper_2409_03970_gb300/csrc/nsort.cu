@@ -93,7 +93,7 @@ template <int NT, int IPT, int DT, bool FINAL>
 __global__ void __launch_bounds__(NT) tile_sort_keys_kernel(const uint32_t *in, uint32_t *out,
                                                             int64_t n, uint32_t *samp) {
   constexpr int TILE = NT * IPT;
-  extern __shared__ __align__(16) unsigned char tile_smem[];   // merge_smem_len(TILE, IPT) words
+  extern __shared__ __align__(16) unsigned char tile_smem[];   // block_smem_len<u32>(NT, IPT) words
   uint32_t *s = reinterpret_cast<uint32_t *>(tile_smem);
   const int tid = threadIdx.x;
   const int64_t base = (int64_t)blockIdx.x * TILE;
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(NT, 2) tile_sort_pairs_kernel(const uint32_t *
   constexpr int TILE = NT * 16;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   uint64_t *s = reinterpret_cast<uint64_t *>(smem_raw);
-  uint32_t *sv = reinterpret_cast<uint32_t *>(s + merge_smem_len<uint64_t>(TILE, 16));
+  uint32_t *sv = reinterpret_cast<uint32_t *>(s + merge_smem_len<uint64_t>(NT * 16, 16));
   const int tid = threadIdx.x;
   const int64_t base = (int64_t)blockIdx.x * TILE;
   const int count = (int)(n - base < TILE ? n - base : TILE);
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(NT, 2) tile_sort_pairs_kernel(const uint32_t *
                                : ~0ull;
     }
   }
-  sort_tile_in_block<NT, 16, Green16Columns>(r, s);
+  sort_tile_in_block<NT, 16, Green16Columns, uint64_t, false>(r, s);
   // every thread passed a barrier after the values were staged
   uint32_t ko[16], vo[16];
 #pragma unroll
@@ -180,7 +180,7 @@ template <int NT, int DT, bool FINAL>
 __global__ void __launch_bounds__(NT) tile_sort_keys64_kernel(const uint64_t *in, uint64_t *out,
                                                               int64_t n, uint64_t *samp) {
   constexpr int TILE = NT * 16;
-  extern __shared__ __align__(16) unsigned char tile64_smem[];   // merge_smem_len<u64>(TILE, 16)
+  extern __shared__ __align__(16) unsigned char tile64_smem[];   // block_smem_len<u64>(NT, 16)
   uint64_t *s = reinterpret_cast<uint64_t *>(tile64_smem);
   const int tid = threadIdx.x;
   const int64_t base = (int64_t)blockIdx.x * TILE;
@@ -724,12 +724,12 @@ constexpr size_t TMA_PMERGE_SMEM = tma_merge_smem(TMA_PMERGE_TILE, true);
 constexpr size_t TMA_K64_SMEM = tma_merge_smem(TMA_K64_TILE, false, 8);
 constexpr int KEYS64_SORT_TILE = KEYS64_SORT_NT * 16;
 constexpr size_t KEYS64_SORT_SMEM =
-    sizeof(uint64_t) * merge_smem_len<uint64_t>(KEYS64_SORT_TILE, 16);
+    sizeof(uint64_t) * block_smem_len<uint64_t>(KEYS64_SORT_NT, 16);
 constexpr int MERGE64_TILE = MERGE64_NT * MERGE64_VT;
 
 constexpr int KEYS_SORT_TILE = KEYS_SORT_NT * KEYS_SORT_IPT;
 constexpr size_t KEYS_SORT_SMEM =
-    sizeof(uint32_t) * merge_smem_len<uint32_t>(KEYS_SORT_TILE, KEYS_SORT_IPT);
+    sizeof(uint32_t) * block_smem_len<uint32_t>(KEYS_SORT_NT, KEYS_SORT_IPT);
 constexpr int PAIRS_SORT_TILE = PAIRS_SORT_NT * 16;
 constexpr int MERGE_TILE = MERGE_NT * MERGE_VT;
 constexpr int PMERGE_TILE = PMERGE_NT * PMERGE_VT;
