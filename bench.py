@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--served-duration", type=float, default=10.0,
                     help="seconds of Poisson arrivals in the served measurement (60 = full)")
     ap.add_argument("--segments", type=int, default=100_000)
+    ap.add_argument("--no-numa-bind", action="store_true",
+                    help="do not restrict the process to the GPU's NUMA node")
     return ap.parse_args()
 
 
@@ -323,25 +325,35 @@ def bench_e2e(nsort, torch, host_in, x, out, tmp, n, code, steps, world, esize=4
     hout = [torch.empty_like(host_in).pin_memory(), torch.empty_like(host_in).pin_memory()]
     ev = lambda: torch.cuda.Event(enable_timing=False)
     up, sorted_, down = [ev(), ev()], [ev(), ev()], [ev(), ev()]
+    tev = lambda: torch.cuda.Event(enable_timing=True)
+    # per-step timing events, read after the loop: upload, sort, download
+    marks = [[tev() for _ in range(6)] for _ in range(2 + ke)]
     torch.cuda.synchronize()
 
     def step(i):
         b = i & 1
+        m = marks[i]
         if i >= 2:
             h2d.wait_event(sorted_[b])        # din[b] no longer read by step i-2
         with torch.cuda.stream(h2d):
+            m[0].record(h2d)
             din[b].copy_(host_in, non_blocking=True)
+            m[1].record(h2d)
             up[b].record(h2d)
         comp.wait_event(up[b])
         if i >= 2:
             comp.wait_event(down[b])          # dout[b] downloaded by step i-2
+        m[2].record(comp)
         rc = nsort.nsort_keys(din[b], dout[b], n, code, tmp, tmp.numel(), comp.cuda_stream)
         if rc != nsort.OK:
             raise nsort.NsortError(rc, "nsort_keys")
+        m[3].record(comp)
         sorted_[b].record(comp)
         d2h.wait_event(sorted_[b])
         with torch.cuda.stream(d2h):
+            m[4].record(d2h)
             hout[b].copy_(dout[b], non_blocking=True)
+            m[5].record(d2h)
             down[b].record(d2h)
 
     for i in range(2):
@@ -357,6 +369,9 @@ def bench_e2e(nsort, torch, host_in, x, out, tmp, n, code, steps, world, esize=4
     torch.cuda.synchronize()
     barrier(world)
     ems = max_over_ranks(t0.elapsed_time(t1) / ke, world)
+    stages = {name: float(np.mean([marks[i][2 * j].elapsed_time(marks[i][2 * j + 1])
+                                   for i in range(2, 2 + ke)]))
+              for j, name in enumerate(("upload_ms", "sort_ms", "download_ms"))}
     # one step alone, start to finish (no overlap between steps)
     s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     s0.record(comp)
@@ -369,6 +384,7 @@ def bench_e2e(nsort, torch, host_in, x, out, tmp, n, code, steps, world, esize=4
     serial_ms = s0.elapsed_time(s1)
     bw = copy_bandwidths(torch, host_in, din[1], dout[1])
     return {"value": world * n / (ems / 1e3) / 1e9, "unit": UNIT, "copy_bandwidths": bw,
+            "stages_in_pipeline": stages,
             "h2d_bytes_per_step": esize * n, "d2h_bytes_per_step": esize * n, "ms_per_step": ems,
             "steps": ke, "pipelined": "3 streams, double-buffered device arrays",
             "one_step_unpipelined_ms": serial_ms}
@@ -745,7 +761,7 @@ def main():
     from paper_2409_03970_gb300 import inputs, nsort
 
     torch.cuda.set_device(local_rank)
-    numa_node = bind_to_gpu_numa_node(torch, local_rank)
+    numa_node = None if args.no_numa_bind else bind_to_gpu_numa_node(torch, local_rank)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
