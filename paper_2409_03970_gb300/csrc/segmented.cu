@@ -5,19 +5,25 @@
 //                            the W_t-input network (W_t = 8 or 16);
 //   small  L <= 32 * IPT     one warp: column sort of IPT keys per lane and
 //                            the warp flip merger (IPT = 8 or 16);
-//   medium L <= TILE         one CTA: tile sort with the active size rounded
+//   medium L <= 16 NT        one CTA: tile sort with the active size rounded
 //                            up to a power of two;
-//   large  L >  TILE         tile sorts of the segment's TILE-key tiles
-//                            (level 0), then one merge level per doubling of
-//                            the run length, each split into TILE-output
-//                            merge tiles with their own merge-path splitters.
+//   large  L >  16 NT        tile sorts of the segment's TILE-key tiles
+//                            (level 0; keys take 32 per thread, TILE = 32 NT,
+//                            pairs 16, TILE = 16 NT), then one merge level per
+//                            doubling of the run length, each split into
+//                            merge tiles of 16 NT outputs with their own
+//                            merge-path splitters.
 // A persistent kernel takes work items from a queue (one atomic counter):
 // [level-0 tiles of all large segments][medium][small batches][tiny
-// batches][level-1 merge tiles][level-2]...  A merge tile of level k waits
-// until every level k-1 item of its segment has finished (a per-segment
-// counter with bounded waiting).  Items are taken in queue order and only
-// wait on items earlier in the queue, which are already held by running
-// CTAs, so the waits always end.
+// batches][level-1 merge tiles][level-2]...  Each large segment counts its
+// finished items and splitter phases.  The CTA that finishes the last item
+// of a level computes the merge-path splitters of all the next level's
+// merge tiles of that segment (a warp per splitter) and counts one more; a
+// merge tile of level k waits until every level k-1 item and the level-k
+// splitter phase of its segment are done (bounded waiting), then reads its
+// two splitters.  Items are taken in queue order and only wait on items
+// earlier in the queue, or on the splitter phase run by the CTA that
+// finished the last of them, so the waits always end.
 //
 // The tunables (block size NT, tiny network width W_t, small-bin IPT, CTAs
 // per SM) come from nsort_segmented_set_config, fed by the autotuner.
@@ -66,10 +72,13 @@ struct Params {
   int *small_list;
   int *medium_list;
   int64_t *slot_base;    // large segment -> first slot of its tiles
-  unsigned long long *done;   // large segment -> finished items
+  int64_t *split;        // slot -> merge-path splitter of that merge tile (current level)
+  unsigned long long *done;   // large segment -> finished items and splitter phases
   int *owner;            // slot -> large segment
   int dt;
-  int tile;              // NT * 16
+  int tile;              // keys per level-0 tile: NT * 32 (keys) or NT * 16 (pairs)
+  int mt;                // outputs per merge tile: NT * 16
+  int r;                 // merge tiles per level-0 tile: tile / mt
   int nt;
   int tiny_w;            // 8 or 16
   int small_ipt;         // 8 or 16
@@ -100,7 +109,7 @@ __global__ void seg_classify_kernel(Params p) {
     p.tiny_list[atomicAdd(&c->n_tiny, 1ull)] = (int)s;
   } else if (L <= 32 * p.small_ipt) {
     p.small_list[atomicAdd(&c->n_small, 1ull)] = (int)s;
-  } else if (L <= p.tile) {
+  } else if (L <= p.mt) {
     p.medium_list[atomicAdd(&c->n_medium, 1ull)] = (int)s;
   } else {
     const int64_t T = (L + p.tile - 1) / p.tile;
@@ -131,7 +140,7 @@ __global__ void seg_plan_kernel(Params p) {
   unsigned long long q = c->q_merge;
   for (int k = 1; k <= maxlv; ++k) {
     c->q_level[k] = q;
-    q += base - c->bucket_base[k];     // tiles of the segments that need k levels or more
+    q += (base - c->bucket_base[k]) * (unsigned long long)p.r;   // r merge tiles per tile
   }
   c->q_level[maxlv + 1] = q;
   c->q_total = q;
@@ -145,7 +154,7 @@ __global__ void seg_owner_kernel(Params p) {
   const int lane = threadIdx.x & 31;
   if (w >= p.nseg || p.ctrl->status != NSORT_OK) return;
   const int64_t L = p.off[w + 1] - p.off[w];
-  if (L <= p.tile) return;
+  if (L <= p.mt) return;
   const int64_t T = (L + p.tile - 1) / p.tile;
   const int64_t g = (int64_t)p.ctrl->bucket_base[ceil_log2(T)] + p.slot_base[w];
   __syncwarp();
@@ -160,13 +169,6 @@ __global__ void seg_owner_kernel(Params p) {
 
 
 
-// Marks one item of segment s finished: every thread fences its own
-// stores, then one thread bumps the counter.
-__device__ __forceinline__ void signal_done(unsigned long long *ctr) {
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) atomicAdd(ctr, 1ull);
-}
 
 template <typename K>
 __device__ __forceinline__ K make_elem(uint32_t key, int pos) {
@@ -256,6 +258,34 @@ __device__ void block_sort_range(const Params &p, void *smem, int64_t base, int 
   }
 }
 
+struct Best32Columns {
+  template <typename K>
+  __device__ __forceinline__ static void sort(K (&r)[32]) { column_sort_net<NET_BEST, 32>(r); }
+};
+
+// Level-0 tile of a large keys-only segment: `count` keys at kin[base],
+// sorted with 32 keys per thread by the keys tile sort's code (the best
+// 32-input network, the warp merge, gapped block merges); stored (mapped
+// back when `final_map`) at kdst[base].
+template <int NT>
+__device__ void tile_sort32_range(const Params &p, void *smem, int64_t base, int count,
+                                  uint32_t *kdst, bool final_map) {
+  uint32_t *s = static_cast<uint32_t *>(smem);
+  const int tid = threadIdx.x;
+  uint32_t r[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    const int e = tid + NT * j;
+    r[j] = e < count ? to_key(p.kin[base + e], p.dt) : 0xFFFFFFFFu;
+  }
+  sort_tile_in_block<NT, 32, Best32Columns, uint32_t, true>(r, s);
+  const int dto = final_map ? p.dt : (int)DT_U32;
+  const int e0 = tid * 32;
+#pragma unroll
+  for (int k = 0; k < 32; ++k)
+    if (e0 + k < count) kdst[base + e0 + k] = from_key(r[k], dto);
+}
+
 // One warp sorts one segment of at most 32*IPT elements.
 template <int IPT, bool PAIRS>
 __device__ void warp_sort_segment(const Params &p, int64_t sid) {
@@ -334,23 +364,95 @@ __device__ __forceinline__ void stage_slices_cg(uint32_t *s, const uint32_t *src
   for (int j = 0; j < VT; ++j) s[sbase + j * (NT + NT / 32)] = t[j];
 }
 
-// Merge tile m of level `level` of large segment sid.
+// Buffer that level `level` of a large segment with P merge levels writes
+// (level 0: the tile sorts): the levels alternate so that level P ends in
+// the output.
+__device__ __forceinline__ bool level_in_tmp(int P, int level) { return ((P - level) & 1) != 0; }
+
+// Item counts of a large segment of L keys: T level-0 tiles, Tm non-empty
+// merge tiles per merge level (the queue holds r * T merge items per level;
+// those past the segment's end do nothing and are not counted), P levels.
+struct SegShape {
+  int64_t off, L, T, Tm;
+  int P;
+};
+__device__ __forceinline__ SegShape seg_shape(const Params &p, int64_t sid) {
+  SegShape g;
+  g.off = p.off[sid];
+  g.L = p.off[sid + 1] - g.off;
+  g.T = (g.L + p.tile - 1) / p.tile;
+  g.Tm = (g.L + p.mt - 1) / p.mt;
+  g.P = ceil_log2(g.T);
+  return g;
+}
+// Counter value once every item of levels 0..k-1 and the splitter phases
+// 1..k-1 are done.
+__device__ __forceinline__ unsigned long long level_done(const SegShape &g, int k) {
+  return (unsigned long long)(g.T + (int64_t)(k - 1) * g.Tm + (k - 1));
+}
+
+// Marks one item of large segment sid, of level `level` (0: a tile sort),
+// finished: the CTA's stores are ordered before one thread's fence and
+// counter update.  If that finished the level (the counter reached
+// level_done(level + 1)), this CTA computes the merge-path splitters of every
+// merge tile of level + 1, one warp per splitter, and counts the phase.
+// Items of the segment's last level are not counted: nothing waits on them.
+template <int NT>
+__device__ void finish_item(const Params &p, int *plan_sh, int64_t sid, int level) {
+  const SegShape g = seg_shape(p, sid);
+  if (level == g.P) return;
+  // the barrier orders every thread's stores before thread 0's fence and
+  // counter update (the release pattern of a grid-wide barrier)
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned long long old = atomicAdd(&p.done[sid], 1ull);
+    const int k = level + 1;
+    *plan_sh = (k <= g.P && old + 1 == level_done(g, k)) ? k : 0;
+  }
+  __syncthreads();
+  const int k = *plan_sh;
+  if (k == 0) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t run = (int64_t)p.tile << (k - 1);
+  const uint32_t *ksrc = (level_in_tmp(g.P, k - 1) ? p.ktmp : p.kout) + g.off;
+  const int64_t s0 = p.slot_base[sid] * p.r;
+  for (int64_t m = threadIdx.x >> 5; m < g.Tm; m += NT / 32) {
+    const int64_t out0 = m * p.mt;
+    const int64_t pair0 = out0 & ~(2 * run - 1);
+    const int64_t la = g.L - pair0 < run ? g.L - pair0 : run;
+    const int64_t rest = g.L - pair0 - run;
+    const int64_t lb = rest <= 0 ? 0 : (rest < run ? rest : run);
+    const int64_t r = out0 == pair0 ? 0
+                                    : merge_path_global_warp<true>(ksrc + pair0, la,
+                                                                   ksrc + pair0 + la, lb,
+                                                                   out0 - pair0, lane);
+    if (lane == 0) p.split[s0 + m] = r;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(&p.done[sid], 1ull);
+  }
+}
+
+// Merge tile m (16 NT outputs) of level `level` of large segment sid.
 template <int NT, bool PAIRS>
-__device__ void merge_tile(const Params &p, void *smem, int64_t *split_sh, int64_t sid, int level,
+__device__ void merge_tile(const Params &p, void *smem, int *plan_sh, int64_t sid, int level,
                            int64_t m) {
   constexpr int VT = 16;
   constexpr int MT = NT * VT;
   const int tid = threadIdx.x;
-  const int lane = tid & 31;
-  const int64_t off = p.off[sid];
-  const int64_t L = p.off[sid + 1] - off;
-  const int64_t T = (L + p.tile - 1) / p.tile;
-  const int P = ceil_log2(T);
-  if (tid == 0)
-    wait_at_least(&p.done[sid], (unsigned long long)level * T, &p.ctrl->status, 2000000000ull);
+  const SegShape g = seg_shape(p, sid);
+  if (m >= g.Tm) return;   // past the segment's end: nothing to merge, not counted
+  const int64_t off = g.off;
+  const int64_t L = g.L;
+  const int P = g.P;
+  if (tid == 0)   // levels 0..level-1 and this level's splitter phase done
+    wait_at_least(&p.done[sid], level_done(g, level) + 1, &p.ctrl->status, 2000000000ull);
   __syncthreads();
-  const bool src_tmp = ((P - level + 1) & 1) != 0;
-  const bool dst_tmp = ((P - level) & 1) != 0;
+  const bool src_tmp = level_in_tmp(P, level - 1);
+  const bool dst_tmp = level_in_tmp(P, level);
   const uint32_t *ksrc = (src_tmp ? p.ktmp : p.kout) + off;
   uint32_t *kdst = (dst_tmp ? p.ktmp : p.kout) + off;
   const int64_t run = (int64_t)p.tile << (level - 1);
@@ -361,20 +463,9 @@ __device__ void merge_tile(const Params &p, void *smem, int64_t *split_sh, int64
   const int64_t rest = L - pair0 - run;
   const int64_t lb = rest <= 0 ? 0 : (rest < run ? rest : run);
   const int64_t pair_end = pair0 + la + lb;
-  const int warp = tid >> 5;
-  if (warp == 0) {
-    const int64_t r = merge_path_global_warp<true>(ksrc + pair0, la, ksrc + pair0 + la, lb,
-                                                   out0 - pair0, lane);
-    if (lane == 0) split_sh[0] = r;
-  } else if (warp == 1) {
-    const int64_t r = out1 == pair_end ? la
-                                       : merge_path_global_warp<true>(ksrc + pair0, la,
-                                                                      ksrc + pair0 + la, lb,
-                                                                      out1 - pair0, lane);
-    if (lane == 0) split_sh[1] = r;
-  }
-  __syncthreads();
-  int64_t a_beg = split_sh[0], a_end = split_sh[1];
+  const int64_t s0 = p.slot_base[sid] * p.r;
+  int64_t a_beg = __ldcg(p.split + s0 + m);
+  int64_t a_end = out1 == pair_end ? la : __ldcg(p.split + s0 + m + 1);
   {
     // keep both slices inside their runs and summing to the tile, whatever the
     // splitters say (they are exact for sorted runs)
@@ -414,14 +505,14 @@ __device__ void merge_tile(const Params &p, void *smem, int64_t *split_sh, int64
     for (int k = 0; k < VT; ++k)
       if (e0 + k < count) vdst[out0 + e0 + k] = sv[pidx<uint32_t>(from[k])];
   }
-  signal_done(&p.done[sid]);
+  finish_item<NT>(p, plan_sh, sid, level);
 }
 
 template <int NT, bool PAIRS>
 __global__ void __launch_bounds__(NT, PAIRS ? 1 : 2) seg_sort_kernel(Params p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ unsigned long long item_sh;
-  __shared__ int64_t split_sh[2];
+  __shared__ int plan_sh;
   const int tid = threadIdx.x;
   Ctrl *c = p.ctrl;
   const unsigned long long q_medium = c->q_medium, q_small = c->q_small, q_tiny = c->q_tiny,
@@ -434,7 +525,8 @@ __global__ void __launch_bounds__(NT, PAIRS ? 1 : 2) seg_sort_kernel(Params p) {
     __syncthreads();
     if (item >= q_total) break;
     if (item < q_medium) {
-      // level 0: tile sort of one tile of a large segment
+      // level 0: tile sort of one tile of a large segment (the whole sort,
+      // key map included, when the segment fits one tile)
       const int sid = p.owner[item];
       const int64_t t = (int64_t)item - p.slot_base[sid];
       const int64_t off = p.off[sid];
@@ -444,8 +536,9 @@ __global__ void __launch_bounds__(NT, PAIRS ? 1 : 2) seg_sort_kernel(Params p) {
       const int count = (int)(L - b0 < p.tile ? L - b0 : p.tile);
       uint32_t *kd = (P & 1) ? p.ktmp : p.kout;
       uint32_t *vd = (P & 1) ? p.vtmp : p.vout;
-      block_sort_range<NT, PAIRS>(p, smem_raw, off + b0, count, NT * 16, kd, vd, false);
-      signal_done(&p.done[sid]);
+      if (PAIRS) block_sort_range<NT, PAIRS>(p, smem_raw, off + b0, count, NT * 16, kd, vd, P == 0);
+      else tile_sort32_range<NT>(p, smem_raw, off + b0, count, kd, P == 0);
+      finish_item<NT>(p, &plan_sh, sid, 0);
     } else if (item < q_small) {
       const int sid = p.medium_list[item - q_medium];
       const int64_t off = p.off[sid];
@@ -470,9 +563,11 @@ __global__ void __launch_bounds__(NT, PAIRS ? 1 : 2) seg_sort_kernel(Params p) {
     } else {
       int k = 1;
       while (k < max_level && item >= c->q_level[k + 1]) ++k;
-      const unsigned long long slot = c->bucket_base[k] + (item - c->q_level[k]);
+      const unsigned long long j = item - c->q_level[k];
+      const unsigned long long slot = c->bucket_base[k] + j / (unsigned)p.r;
       const int sid = p.owner[slot];
-      merge_tile<NT, PAIRS>(p, smem_raw, split_sh, sid, k, (int64_t)slot - p.slot_base[sid]);
+      const int64_t m = ((int64_t)slot - p.slot_base[sid]) * p.r + (int64_t)(j % (unsigned)p.r);
+      merge_tile<NT, PAIRS>(p, smem_raw, &plan_sh, sid, k, m);
     }
   }
 }
@@ -480,7 +575,7 @@ __global__ void __launch_bounds__(NT, PAIRS ? 1 : 2) seg_sort_kernel(Params p) {
 // ---- host side -------------------------------------------------------------
 
 struct Layout {
-  size_t ctrl, keys, vals, tiny, small, medium, slot, done, owner, total;
+  size_t ctrl, keys, vals, tiny, small, medium, slot, done, owner, split, total;
 };
 
 Layout layout(uint64_t n, uint64_t nseg, bool pairs) {
@@ -500,6 +595,7 @@ Layout layout(uint64_t n, uint64_t nseg, bool pairs) {
   l.slot = take(nseg * 8);
   l.done = take(nseg * 8);
   l.owner = take((2 * (n / MIN_TILE) + 2) * 4);
+  l.split = take((2 * (n / MIN_TILE) + 2) * 2 * 8);   // up to two merge tiles per slot
   l.total = o;
   return l;
 }
@@ -511,8 +607,10 @@ template <int NT, bool PAIRS>
 size_t smem_bytes() {
   using K = typename std::conditional<PAIRS, uint64_t, uint32_t>::type;
   const size_t tile_b = sizeof(K) * merge_smem_len<K>(NT * 16, 16);
+  const size_t tile32_b = PAIRS ? 0 : sizeof(uint32_t) * block_smem_len<uint32_t>(NT, 32);
   const size_t merge_b = sizeof(uint32_t) * 2 * merge_smem_len<uint32_t>(NT * 16, 16);
-  return tile_b > merge_b ? tile_b : merge_b;
+  size_t m = tile_b > merge_b ? tile_b : merge_b;
+  return m > tile32_b ? m : tile32_b;
 }
 
 template <int NT, bool PAIRS>
@@ -605,9 +703,12 @@ extern "C" int nsort_segmented(const void *d_keys_in, void *d_keys_out, const ui
   p.slot_base = reinterpret_cast<int64_t *>(t + l.slot);
   p.done = reinterpret_cast<unsigned long long *>(t + l.done);
   p.owner = reinterpret_cast<int *>(t + l.owner);
+  p.split = reinterpret_cast<int64_t *>(t + l.split);
   p.dt = dtype;
   p.nt = cfg.block_threads;
-  p.tile = cfg.block_threads * 16;
+  p.mt = cfg.block_threads * 16;
+  p.tile = pairs ? p.mt : cfg.block_threads * 32;
+  p.r = p.tile / p.mt;
   p.tiny_w = cfg.tiny_width;
   p.small_ipt = cfg.small_ipt;
   cudaStream_t st = static_cast<cudaStream_t>(stream);

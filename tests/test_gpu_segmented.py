@@ -38,7 +38,8 @@ def dev(a, dtype=np.int32):
 def mixed_offsets(seed, extra=()):
     """Lengths covering every bin and its edges, plus log-uniform ones."""
     edges = [0, 1, 2, 7, 8, 9, 15, 16, 17, 255, 256, 257, 511, 512, 513, 4095, 4096, 4097,
-             8191, 8192, 8193, 16384, 16385, 40000, 65536, 100_003]
+             8191, 8192, 8193, 16383, 16384, 16385, 32767, 32768, 32769, 40000, 65536,
+             100_003]
     rnd = np.diff(inputs.segment_offsets(300, seed=seed, max_len=65536))
     lens = np.array(list(edges) + list(rnd) + list(extra), dtype=np.int64)
     rng_perm = inputs.counter_u64(seed, 7, 0, lens.size).argsort()
