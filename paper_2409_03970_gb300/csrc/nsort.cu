@@ -851,6 +851,29 @@ static void launch_tile_sort_keys(const uint32_t *in, uint32_t *out, int64_t n, 
 #undef NSORT_TSK
 }
 
+// A whole sort in one CTA of NT threads x 16 keys (a tile of 16 NT keys).
+template <int NT>
+static void small_sort_nt(const uint32_t *in, uint32_t *out, int64_t n, int dt, cudaStream_t st) {
+  constexpr size_t smem = sizeof(uint32_t) * block_smem_len<uint32_t>(NT, 16);
+  static_assert(smem <= 48 * 1024, "fits the default dynamic shared memory");
+  if (dt == DT_U32) tile_sort_keys_kernel<NT, 16, DT_U32, true><<<1, NT, smem, st>>>(in, out, n, nullptr);
+  else if (dt == DT_I32) tile_sort_keys_kernel<NT, 16, DT_I32, true><<<1, NT, smem, st>>>(in, out, n, nullptr);
+  else tile_sort_keys_kernel<NT, 16, DT_F32, true><<<1, NT, smem, st>>>(in, out, n, nullptr);
+}
+
+// A sort that fits one tile of a smaller configuration takes the smallest
+// of 512, 2048 and 8192 keys (32, 128 or 512 threads x 16 keys) that holds
+// n, so that a short array does not pay for a full 16384-key tile.  Returns
+// false when n needs the full tile.
+static bool launch_small_sort(const uint32_t *in, uint32_t *out, int64_t n, int dt,
+                              cudaStream_t st) {
+  if (n <= 512) small_sort_nt<32>(in, out, n, dt, st);
+  else if (n <= 2048) small_sort_nt<128>(in, out, n, dt, st);
+  else if (n <= 8192) small_sort_nt<512>(in, out, n, dt, st);
+  else return false;
+  return true;
+}
+
 static void launch_merge_keys(const uint32_t *src, uint32_t *dst, int64_t n, int64_t run,
                               const int64_t *split, int dt_out, unsigned grid, cudaStream_t st) {
 #define NSORT_MK(DT) \
@@ -1110,8 +1133,9 @@ int sort_keys_impl(const uint32_t *in, uint32_t *out, int64_t n, int dt, void *t
   const int64_t tiles = (n + p.sort_tile - 1) / p.sort_tile;
   {
     TraceScope tr(TK_TILE_SORT_KEYS, st);
-    launch_tile_sort_keys(in, bufs[cur], n, dt, p.merge_passes == 0, (unsigned)tiles,
-                          tma ? samp : nullptr, st);
+    if (p.merge_passes > 0 || !launch_small_sort(in, bufs[cur], n, dt, st))
+      launch_tile_sort_keys(in, bufs[cur], n, dt, p.merge_passes == 0, (unsigned)tiles,
+                            tma ? samp : nullptr, st);
   }
   int rc = launch_status("tile_sort_keys");
   for (int pass = 0; rc == NSORT_OK && pass < p.merge_passes; ++pass) {
