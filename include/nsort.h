@@ -128,7 +128,8 @@ int nsort_pairs(const void *d_keys_in, const uint32_t *d_vals_in,
  * length on the device) and one persistent kernel that takes segments from
  * a work queue: one thread per segment of at most `tiny_width` keys, one
  * warp per segment of at most 32 x `small_ipt`, one CTA per segment of at
- * most one tile, and tile sorts plus merge levels for longer ones.  Every
+ * most 16 x block_threads keys, and tile sorts (32 keys per thread for keys
+ * only, 16 with values) plus merge levels for longer ones.  Every
  * step is stream-ordered with no host synchronisation, so the call can be
  * captured into a CUDA graph.  Scratch:
  * nsort_temp_bytes(NSORT_KIND_SEGMENTED[_PAIRS], n, nseg, dtype), 256-byte
@@ -144,7 +145,9 @@ int nsort_segmented(const void *d_keys_in, void *d_keys_out,
 
 /* Tunables of nsort_segmented, set by the autotuner (process-wide). */
 typedef struct {
-    int block_threads;   /* 256 or 512: persistent CTA size; tile = 16 x block_threads keys */
+    int block_threads;   /* 256 or 512: persistent CTA size; one-CTA segments up to
+                            16 x block_threads keys, longer ones in tiles of 32 (keys)
+                            or 16 (pairs) x block_threads */
     int tiny_width;      /* 8 or 16: network width of the one-thread bin */
     int small_ipt;       /* 8 or 16: keys per lane of the one-warp bin */
     int blocks_per_sm;   /* persistent CTAs per SM; 0 = as many as fit */
