@@ -408,7 +408,7 @@ def time_sort(nsort, torch, fn, reps: int = 5, warm: int = 2):
 
 def bench_configs(nsort, torch):
     """The other plain-sort configurations: 2^28 int32 / float32 keys over
-    several distributions, 2^27 stable float32 key / uint32 value pairs
+    the five distributions (uniform, sorted, reverse, 16 distinct, Zipf), 2^27 stable float32 key / uint32 value pairs
     (Normal(0,1) with 0.1% IEEE specials, payload = index), and 2^27 64-bit
     keys."""
     from paper_2409_03970_gb300 import inputs
@@ -416,8 +416,7 @@ def bench_configs(nsort, torch):
     out = {}
     tmp = nsort.scratch(nsort.KIND_KEYS, n)
     ko = torch.empty(n, dtype=torch.int32, device="cuda")
-    for dt, dist in (("i32", "uniform"), ("f32", "uniform"), ("f32", "sorted"),
-                     ("f32", "reverse"), ("f32", "dup16")):
+    for dt, dist in [(d, x) for d in ("i32", "f32") for x in inputs.DISTRIBUTIONS]:
         x = torch.from_numpy(inputs.keys(n, dt, dist, seed=0).view(np.int32)).cuda()
         code = {"i32": nsort.I32, "f32": nsort.F32}[dt]
         ms = time_sort(nsort, torch,
