@@ -71,6 +71,18 @@ def test_keys_all_dtypes_distributions(ns, dt, dist, n):
     np.testing.assert_array_equal(gpu_sort(ns, x, dt), oracle.sort_keys(x, dt))
 
 
+@pytest.mark.parametrize("dt", ["u32", "i32", "f32"])
+@pytest.mark.parametrize("n", [1, 300, 512, 513, 2048, 2049, 5000, 8192])
+def test_keys_small_single_cta_sorts(ns, dt, n):
+    """Sorts of at most 8192 keys run in one CTA of 512, 2048 or 8192 keys;
+    every dtype at each size edge, misaligned and in place too."""
+    x = inputs.keys(n, dt, "dup16" if n % 2 else "uniform", seed=n)
+    want = oracle.sort_keys(x, dt)
+    np.testing.assert_array_equal(gpu_sort(ns, x, dt), want)
+    np.testing.assert_array_equal(gpu_sort(ns, x, dt, offset=1), want)
+    np.testing.assert_array_equal(gpu_sort(ns, x, dt, inplace=True), want)
+
+
 def test_keys_f32_specials_and_nan_payloads(ns):
     k, _ = inputs.normal_pairs(300_000, seed=2, special_per_mille=100)
     extra = np.array([0xFFFFFFFF, 0xFFC00001, 0xFF800001, 0x7F800001, 0x7FBFFFFF,
