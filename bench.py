@@ -77,14 +77,26 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(x: float, world: int) -> float:
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    """The largest x over all ranks (the slowest rank's time).  device is
+    where the one-element reduction tensor lives: "cuda" under NCCL, "cpu"
+    under gloo."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_throughput(ms_local: float, n_per_rank: int, world: int,
+                       device: str = "cuda") -> tuple[float, float]:
+    """Whole-job rate of `world` replicas that each sorted n_per_rank keys in
+    ms_local milliseconds: (max-over-ranks ms, GKeys/s of all ranks over that
+    time)."""
+    ms = max_over_ranks(ms_local, world, device)
+    return ms, world * n_per_rank / (ms / 1e3) / 1e9
 
 
 # ---- clocks ------------------------------------------------------------------
@@ -368,7 +380,7 @@ def bench_e2e(nsort, torch, host_in, x, out, tmp, n, code, steps, world, esize=4
     t1.record(d2h)
     torch.cuda.synchronize()
     barrier(world)
-    ems = max_over_ranks(t0.elapsed_time(t1) / ke, world)
+    ems, e2e_value = replica_throughput(t0.elapsed_time(t1) / ke, n, world)
     stages = {name: float(np.mean([marks[i][2 * j].elapsed_time(marks[i][2 * j + 1])
                                    for i in range(2, 2 + ke)]))
               for j, name in enumerate(("upload_ms", "sort_ms", "download_ms"))}
@@ -383,7 +395,7 @@ def bench_e2e(nsort, torch, host_in, x, out, tmp, n, code, steps, world, esize=4
     torch.cuda.synchronize()
     serial_ms = s0.elapsed_time(s1)
     bw = copy_bandwidths(torch, host_in, din[1], dout[1])
-    return {"value": world * n / (ems / 1e3) / 1e9, "unit": UNIT, "copy_bandwidths": bw,
+    return {"value": e2e_value, "unit": UNIT, "copy_bandwidths": bw,
             "stages_in_pipeline": stages,
             "h2d_bytes_per_step": esize * n, "d2h_bytes_per_step": esize * n, "ms_per_step": ems,
             "steps": ke, "pipelined": "3 streams, double-buffered device arrays",
@@ -832,8 +844,7 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     barrier(world)
-    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
-    value = world * n / (ms / 1e3) / 1e9
+    ms, value = replica_throughput(e0.elapsed_time(e1) / args.steps, n, world)
     # per-kernel durations: the same steps once more with the library's
     # tracing on (CUDA events around every launch on its stream).  Tracing
     # puts events between the kernels, which costs time and undoes the
