@@ -392,6 +392,21 @@ __device__ __forceinline__ PairTile pair_tile_from(int64_t t, int64_t n, int64_t
   return g;
 }
 
+// Splitter of tile v of the pair-aligned tiling (what the partition kernels
+// write to split[v]), found by a group of W lanes of one warp.
+template <int W, typename K>
+__device__ __forceinline__ int64_t tile_corank_group(const K *src, int64_t n, int64_t run,
+                                                     int64_t tpp, int tile, int64_t v, int glane,
+                                                     unsigned gmask) {
+  const int64_t pair = v / tpp;
+  const int64_t j = v - pair * tpp;
+  const int64_t pair0 = pair * 2 * run;
+  const int64_t la = n - pair0 < run ? n - pair0 : run;
+  const int64_t rest = n - pair0 - run;
+  const int64_t lb = rest <= 0 ? 0 : (rest < run ? rest : run);
+  return merge_path_global_group<W>(src + pair0, la, src + pair0 + la, lb, j * tile, glane, gmask);
+}
+
 // Splitters for the pair-aligned tiling, one thread per tile.
 __global__ void partition_pairs_kernel(const uint32_t *__restrict__ src, int64_t n, int64_t run,
                                        int64_t tpp, int tile, int64_t num_tiles,
@@ -521,7 +536,13 @@ __device__ __forceinline__ void issue_tile(const K *__restrict__ src,
 // with warp-level synchronisation only.  Lane 0 of warp 0 loads the
 // splitters of the tile after next one iteration early.  K is the key word:
 // 32-bit keys (keys or pairs) or 64-bit keys (keys only).
-template <int NT, int VT, int DT_OUT, bool PAIRS, typename K = uint32_t>
+// SELF: a self-partitioned pass (split unused), launched only when no CTA has
+// more than two tiles.  Warp 0 then finds the splitters itself, which saves
+// the separate partition launch and its chain of dependent loads on passes
+// too small to hide them: the first tile's start and end (lanes 0-15 and
+// 16-31 at once, 16-ary searches) before its copies are issued, then the
+// second tile's while those copies land.
+template <int NT, int VT, int DT_OUT, bool PAIRS, typename K = uint32_t, bool SELF = false>
 __global__ void __launch_bounds__(NT, PAIRS ? 3 : 4) merge_tma_kernel(
     const K *__restrict__ src, const uint32_t *__restrict__ vsrc, K *__restrict__ dst,
     uint32_t *__restrict__ vdst, int64_t n, int64_t run, int64_t tpp, int64_t num_tiles,
@@ -558,21 +579,43 @@ __global__ void __launch_bounds__(NT, PAIRS ? 3 : 4) merge_tma_kernel(
   // ended, on data still in L2)
   auto tile_of = [&](int64_t i) { return reverse ? num_tiles - 1 - i : i; };
   int64_t pf0 = 0, pf1 = 0;   // thread 0: splitters of loop index t + G
+  [[maybe_unused]] int64_t own0 = 0, own1 = 0;   // SELF: the first tile's splitters (warp 0)
+  // Self-partitioned: warp 0 finds the start splitter of tile u (lanes 0-15)
+  // and of the next tile, u's end (lanes 16-31).
+  [[maybe_unused]] auto self_split = [&](int64_t i, int64_t &s0, int64_t &s1) {
+    const int64_t v = tile_of(i) + (lane >> 4);
+    const unsigned gmask = 0xFFFFu << (lane & 16);
+    int64_t c = 0;
+    if (v < num_tiles) c = tile_corank_group<16>(src, n, run, tpp, TILE, v, lane & 15, gmask);
+    s1 = __shfl_sync(0xffffffffu, c, 16);
+    s0 = c;
+  };
+  if constexpr (SELF) {
+    if (warp == 0 && t < num_tiles) self_split(t, own0, own1);
+  }
   if (tid == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     fence_mbar_init();
     if (t < num_tiles) {
       const int64_t u = tile_of(t);
-      desc[0] = pair_tile_from(u, n, run, tpp, TILE, split[u],
-                               u + 1 < num_tiles ? split[u + 1] : 0);
+      if constexpr (SELF)
+        desc[0] = pair_tile_from(u, n, run, tpp, TILE, own0, own1);
+      else
+        desc[0] = pair_tile_from(u, n, run, tpp, TILE, split[u],
+                                 u + 1 < num_tiles ? split[u + 1] : 0);
       issue_tile(src, PAIRS ? vsrc : nullptr, n_al, desc[0], in_buf[0], vin_buf[0], &bar[0]);
     }
-    if (t + G < num_tiles) {
-      const int64_t u = tile_of(t + G);
-      pf0 = split[u];
-      pf1 = u + 1 < num_tiles ? split[u + 1] : 0;
+    if constexpr (!SELF) {
+      if (t + G < num_tiles) {
+        const int64_t u = tile_of(t + G);
+        pf0 = split[u];
+        pf1 = u + 1 < num_tiles ? split[u + 1] : 0;
+      }
     }
+  }
+  if constexpr (SELF) {
+    if (warp == 0 && t + G < num_tiles) self_split(t + G, pf0, pf1);
   }
   __syncthreads();
   bool ok = true;
@@ -595,11 +638,13 @@ __global__ void __launch_bounds__(NT, PAIRS ? 3 : 4) merge_tma_kernel(
       desc[b ^ 1] = pair_tile_from(tile_of(tn), n, run, tpp, TILE, pf0, pf1);
       issue_tile(src, PAIRS ? vsrc : nullptr, n_al, desc[b ^ 1], in_buf[b ^ 1], vin_buf[b ^ 1],
                  &bar[b ^ 1]);
-      const int64_t tp = tn + G;
-      if (tp < num_tiles) {
-        const int64_t u = tile_of(tp);
-        pf0 = split[u];
-        pf1 = u + 1 < num_tiles ? split[u + 1] : 0;
+      if constexpr (!SELF) {   // (a self-partitioned pass has at most two tiles per CTA)
+        const int64_t tp = tn + G;
+        if (tp < num_tiles) {
+          const int64_t u = tile_of(tp);
+          pf0 = split[u];
+          pf1 = u + 1 < num_tiles ? split[u + 1] : 0;
+        }
       }
     }
     const PairTile g = desc[b];
@@ -938,9 +983,12 @@ static void launch_partition(const uint32_t *src, int64_t n, int64_t run, const 
 
 template <int NT, int VT, bool PAIRS>
 static void tma_merge_attrs(size_t smem) {
-  const void *fns[3] = {(const void *)merge_tma_kernel<NT, VT, DT_U32, PAIRS>,
+  const void *fns[6] = {(const void *)merge_tma_kernel<NT, VT, DT_U32, PAIRS>,
                         (const void *)merge_tma_kernel<NT, VT, DT_I32, PAIRS>,
-                        (const void *)merge_tma_kernel<NT, VT, DT_F32, PAIRS>};
+                        (const void *)merge_tma_kernel<NT, VT, DT_F32, PAIRS>,
+                        (const void *)merge_tma_kernel<NT, VT, DT_U32, PAIRS, uint32_t, true>,
+                        (const void *)merge_tma_kernel<NT, VT, DT_I32, PAIRS, uint32_t, true>,
+                        (const void *)merge_tma_kernel<NT, VT, DT_F32, PAIRS, uint32_t, true>};
   for (const void *f : fns) {   // opt in to the dynamic shared memory; prefer it over L1
     cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
@@ -958,10 +1006,13 @@ static int tma_merge_grid(int64_t tiles, int kind) {
     int sms = 0, occ = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (kind == 2) {
-      const void *fns[3] = {
+      const void *fns[6] = {
           (const void *)merge_tma_kernel<TMA_K64_NT, TMA_K64_VT, DT_U64, false, uint64_t>,
           (const void *)merge_tma_kernel<TMA_K64_NT, TMA_K64_VT, DT_I64, false, uint64_t>,
-          (const void *)merge_tma_kernel<TMA_K64_NT, TMA_K64_VT, DT_F64, false, uint64_t>};
+          (const void *)merge_tma_kernel<TMA_K64_NT, TMA_K64_VT, DT_F64, false, uint64_t>,
+          (const void *)merge_tma_kernel<TMA_K64_NT, TMA_K64_VT, DT_U64, false, uint64_t, true>,
+          (const void *)merge_tma_kernel<TMA_K64_NT, TMA_K64_VT, DT_I64, false, uint64_t, true>,
+          (const void *)merge_tma_kernel<TMA_K64_NT, TMA_K64_VT, DT_F64, false, uint64_t, true>};
       for (const void *f : fns) {
         cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TMA_K64_SMEM);
         cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
@@ -997,16 +1048,23 @@ static void launch_merge_tma(const uint32_t *src, const uint32_t *vsrc, uint32_t
   const int tile = pairs ? TMA_PMERGE_TILE : TMA_MERGE_TILE;
   int64_t tpp = 0;
   const int64_t tiles = pair_tiles(n, run, tile, &tpp);
-  {
+  const unsigned grid = (unsigned)tma_merge_grid(tiles, pairs ? 1 : 0);
+  if (tiles > 2 * (int64_t)grid) {
     TraceScope tr(TK_PARTITION, st);
     launch_pdl(partition_sampled_kernel<uint32_t>, (unsigned)((tiles + 255) / 256), 256, 0, st,
                src, samp_in, n, run, tpp, tile, tiles, split);
+  } else {
+    split = nullptr;   // at most two tiles per CTA: each finds its own splitters
   }
-  const unsigned grid = (unsigned)tma_merge_grid(tiles, pairs ? 1 : 0);
   TraceScope tr(pairs ? TK_MERGE_PAIRS : TK_MERGE_KEYS, st);
+#define NSORT_MT1(NT, VT, DT, P, SMEM, SELF)                                                   \
+  launch_pdl(merge_tma_kernel<NT, VT, DT, P, uint32_t, SELF>, grid, NT, SMEM, st, src, vsrc, dst, \
+             vdst, n, run, tpp, tiles, split, status, samp_out, reverse)
 #define NSORT_MT(NT, VT, DT, P, SMEM)                                                        \
-  launch_pdl(merge_tma_kernel<NT, VT, DT, P, uint32_t>, grid, NT, SMEM, st, src, vsrc, dst, vdst, \
-             n, run, tpp, tiles, split, status, samp_out, reverse)
+  do {                                                                                       \
+    if (split) NSORT_MT1(NT, VT, DT, P, SMEM, false);                                       \
+    else NSORT_MT1(NT, VT, DT, P, SMEM, true);                                              \
+  } while (0)
   if (!pairs) {
     if (dt_out == DT_U32) NSORT_MT(TMA_MERGE_NT, TMA_MERGE_VT, DT_U32, false, TMA_MERGE_SMEM);
     else if (dt_out == DT_I32) NSORT_MT(TMA_MERGE_NT, TMA_MERGE_VT, DT_I32, false, TMA_MERGE_SMEM);
@@ -1017,6 +1075,7 @@ static void launch_merge_tma(const uint32_t *src, const uint32_t *vsrc, uint32_t
     else NSORT_MT(TMA_PMERGE_NT, TMA_PMERGE_VT, DT_F32, true, TMA_PMERGE_SMEM);
   }
 #undef NSORT_MT
+#undef NSORT_MT1
 }
 
 // ---- 64-bit keys -------------------------------------------------------------
@@ -1041,23 +1100,31 @@ static void launch_merge_tma64(const uint64_t *src, uint64_t *dst, int64_t n, in
                                uint64_t *samp_out, int reverse, cudaStream_t st) {
   int64_t tpp = 0;
   const int64_t tiles = pair_tiles(n, run, TMA_K64_TILE, &tpp);
-  {
+  const unsigned grid = (unsigned)tma_merge_grid(tiles, 2);
+  if (tiles > 2 * (int64_t)grid) {
     TraceScope tr(TK_PARTITION, st);
     launch_pdl(partition_sampled_kernel<uint64_t>, (unsigned)((tiles + 255) / 256), 256, 0, st,
                src, samp_in, n, run, tpp, TMA_K64_TILE, tiles, split);
+  } else {
+    split = nullptr;   // at most two tiles per CTA: each finds its own splitters
   }
-  const unsigned grid = (unsigned)tma_merge_grid(tiles, 2);
   TraceScope tr(TK_MERGE_KEYS64, st);
   const uint32_t *no_vals = nullptr;
   uint32_t *no_vals_out = nullptr;
+#define NSORT_MT64S(DT, SELF)                                                                \
+  launch_pdl(merge_tma_kernel<TMA_K64_NT, TMA_K64_VT, DT, false, uint64_t, SELF>, grid,       \
+             TMA_K64_NT, TMA_K64_SMEM, st, src, no_vals, dst, no_vals_out, n, run, tpp, tiles, \
+             split, status, samp_out, reverse)
 #define NSORT_MT64(DT)                                                                       \
-  launch_pdl(merge_tma_kernel<TMA_K64_NT, TMA_K64_VT, DT, false, uint64_t>, grid, TMA_K64_NT, \
-             TMA_K64_SMEM, st, src, no_vals, dst, no_vals_out, n, run, tpp, tiles, split,      \
-             status, samp_out, reverse)
+  do {                                                                                       \
+    if (split) NSORT_MT64S(DT, false);                                                       \
+    else NSORT_MT64S(DT, true);                                                              \
+  } while (0)
   if (dt_out == DT_U64) NSORT_MT64(DT_U64);
   else if (dt_out == DT_I64) NSORT_MT64(DT_I64);
   else NSORT_MT64(DT_F64);
 #undef NSORT_MT64
+#undef NSORT_MT64S
 }
 
 // Staged-load merge pass over 64-bit keys, for output buffers that are not

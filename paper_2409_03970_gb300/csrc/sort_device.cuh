@@ -255,6 +255,34 @@ __device__ __forceinline__ int64_t merge_path_global_warp(const uint32_t *A, int
   return lo;
 }
 
+// The same search by a group of W lanes of one warp (W a power of two;
+// glane = lane within the group, gmask = the group's lanes), on keys of any
+// word size: each round the W lanes test W evenly spaced candidates, which
+// shrinks the interval by a factor of about W + 1.  All lanes of the group
+// must call it with the same arguments; all get the result.
+template <int W, typename K>
+__device__ __forceinline__ int64_t merge_path_global_group(const K *A, int64_t na, const K *B,
+                                                           int64_t nb, int64_t diag, int glane,
+                                                           unsigned gmask) {
+  int64_t lo = diag - nb > 0 ? diag - nb : 0;
+  int64_t hi = diag < na ? diag : na;
+  while (lo < hi) {                                  // answer in [lo, hi]
+    const int64_t step = (hi - lo + W) / (W + 1);    // >= 1
+    const int64_t q = lo + (int64_t)(glane + 1) * step - 1;
+    bool p = false;                                  // p: A[q] goes before the diagonal
+    if (q < hi) p = __ldg(A + q) <= __ldg(B + (diag - 1 - q));
+    const int c = __popc(__ballot_sync(gmask, p) & gmask);   // true probes form a prefix
+    int64_t nhi = hi;
+    if (c < W) {
+      const int64_t qc = lo + (int64_t)(c + 1) * step - 1;
+      if (qc < hi) nhi = qc;
+    }
+    lo = lo + (int64_t)c * step;
+    hi = nhi;
+  }
+  return lo;
+}
+
 // Merge path on unpadded shared memory: A and B are separate contiguous
 // runs (the merge pass stages them with bulk copies, which cannot pad).
 template <typename K>

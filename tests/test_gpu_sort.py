@@ -71,6 +71,32 @@ def test_keys_all_dtypes_distributions(ns, dt, dist, n):
     np.testing.assert_array_equal(gpu_sort(ns, x, dt), oracle.sort_keys(x, dt))
 
 
+# Where the merge passes find their splitters: the persistent merge grid has
+# 152 SMs x 4 CTAs = 608 CTAs on GB300.  Passes with at most one tile per CTA
+# (keys: 608 x 3968 = 2,412,544 keys) or two (4,825,088) find their own
+# splitters inside the merge kernel; larger passes launch the partition
+# kernel.  The sizes straddle both boundaries.
+MODE_SIZES_KEYS = [2_412_544, 2_412_545, 3_000_017, 4_825_088, 4_825_089, 5_000_011]
+MODE_SIZES_PAIRS = [1_167_360, 1_167_361, 2_334_720, 2_334_721]
+
+
+@pytest.mark.parametrize("dist", ["uniform", "sorted", "dup16"])
+@pytest.mark.parametrize("n", MODE_SIZES_KEYS)
+def test_keys_splitter_modes(ns, n, dist):
+    x = inputs.keys(n, "f32", dist, seed=n)
+    np.testing.assert_array_equal(gpu_sort(ns, x, "f32"), oracle.sort_keys(x, "f32"))
+
+
+@pytest.mark.parametrize("n", MODE_SIZES_PAIRS)
+def test_pairs_splitter_modes(ns, n):
+    k = inputs.keys(n, "i32", "dup16", seed=n)
+    v = inputs.counter_u32(5, 6, 0, n)
+    ko, vo = gpu_pairs(ns, k, v, "i32")
+    wk, wv = oracle.sort_pairs(k, v, "i32")
+    np.testing.assert_array_equal(ko, wk)
+    np.testing.assert_array_equal(vo, wv)
+
+
 @pytest.mark.parametrize("dt", ["u32", "i32", "f32"])
 @pytest.mark.parametrize("n", [1, 300, 512, 513, 2048, 2049, 5000, 8192])
 def test_keys_small_single_cta_sorts(ns, dt, n):

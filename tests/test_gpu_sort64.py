@@ -77,6 +77,15 @@ def test_keys64_f64_totalorder_table(ns, golden):
     assert first == sorted(first)
 
 
+@pytest.mark.parametrize("n", [1_167_360, 1_167_361, 2_334_720, 2_334_721])
+def test_keys64_splitter_modes(ns, n):
+    """Sizes at the boundaries between merge passes that find their own
+    splitters (at most one, or two, 1920-key tiles per CTA of the 608-CTA
+    grid) and passes that launch the partition kernel."""
+    x = inputs.keys64(n, "i64", "dup16", seed=n)
+    assert np.array_equal(gpu_sort64(ns, x, "i64"), oracle.sort_keys64(x, "i64"))
+
+
 @pytest.mark.parametrize("n", [4096, 70_000, 1 << 19])
 def test_keys64_in_place(ns, n):
     x = inputs.keys64(n, "i64", "uniform", seed=9)
