@@ -245,16 +245,26 @@ __device__ void block_sort_range(const Params &p, void *smem, int64_t base, int 
 #pragma unroll
     for (int k = 0; k < 16; ++k) vo[k] = e0 + k < count ? p.vin[base + elem_pos(r[k])] : 0u;
   }
-  if (PAIRS) __syncthreads();   // every value gathered before any is overwritten in place
   const int dto = final_map ? p.dt : (int)DT_U32;
+  // thread t holds sorted elements [16t, 16t + 16): staged in shared memory
+  // (padded; keys, then values for pairs) so that the global stores are
+  // coalesced whatever the segment's alignment
+  uint32_t *sk = reinterpret_cast<uint32_t *>(smem);
+  uint32_t *sv = sk + padded_len<uint32_t>(m);
+  __syncthreads();   // s is no longer read; every value gathered (vdst may alias vin)
   if (e0 < m) {
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
       if (e0 + k < count) {
-        kdst[base + e0 + k] = from_key(elem_key(r[k]), dto);
-        if (PAIRS) vdst[base + e0 + k] = vo[k];
+        sk[pidx<uint32_t>(e0 + k)] = from_key(elem_key(r[k]), dto);
+        if (PAIRS) sv[pidx<uint32_t>(e0 + k)] = vo[k];
       }
     }
+  }
+  __syncthreads();
+  for (int e = tid; e < count; e += NT) {
+    kdst[base + e] = sk[pidx<uint32_t>(e)];
+    if (PAIRS) vdst[base + e] = sv[pidx<uint32_t>(e)];
   }
 }
 
@@ -280,10 +290,19 @@ __device__ void tile_sort32_range(const Params &p, void *smem, int64_t base, int
   }
   sort_tile_in_block<NT, 32, Best32Columns, uint32_t, true>(r, s);
   const int dto = final_map ? p.dt : (int)DT_U32;
+  // thread t holds tile elements [32t, 32t + 32): staged in shared memory
+  // (padded, conflict-free both ways) so that the global stores are
+  // coalesced whatever the segment's alignment
   const int e0 = tid * 32;
+  __syncthreads();   // every thread is done reading s in the last merge level
 #pragma unroll
-  for (int k = 0; k < 32; ++k)
-    if (e0 + k < count) kdst[base + e0 + k] = from_key(r[k], dto);
+  for (int k = 0; k < 32; ++k) s[pidx<uint32_t>(e0 + k)] = r[k];
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    const int e = tid + NT * j;
+    if (e < count) kdst[base + e] = from_key(s[pidx<uint32_t>(e)], dto);
+  }
 }
 
 // One warp sorts one segment of at most 32*IPT elements.
@@ -496,14 +515,30 @@ __device__ void merge_tile(const Params &p, void *smem, int *plan_sh, int64_t si
   serial_merge<VT, PAIRS>(sk, ai, na, na + diag - ai, count, o, from);
   const int dto = level == P ? p.dt : (int)DT_U32;
   const int e0 = tid * VT;
-#pragma unroll
-  for (int k = 0; k < VT; ++k)
-    if (e0 + k < count) kdst[out0 + e0 + k] = from_key(o[k], dto);
+  uint32_t ov[VT];
   if (PAIRS) {
-    uint32_t *vdst = (dst_tmp ? p.vtmp : p.vout) + off;
 #pragma unroll
-    for (int k = 0; k < VT; ++k)
-      if (e0 + k < count) vdst[out0 + e0 + k] = sv[pidx<uint32_t>(from[k])];
+    for (int k = 0; k < VT; ++k) ov[k] = sv[pidx<uint32_t>(from[k])];
+  }
+  // thread t holds outputs [VT t, VT t + VT): staged in shared memory so
+  // that the global stores are coalesced
+  __syncthreads();   // every thread is done reading the staged slices
+#pragma unroll
+  for (int k = 0; k < VT; ++k) {
+    if (e0 + k < count) {
+      sk[pidx<uint32_t>(e0 + k)] = from_key(o[k], dto);
+      if (PAIRS) sv[pidx<uint32_t>(e0 + k)] = ov[k];
+    }
+  }
+  __syncthreads();
+  uint32_t *vdst = PAIRS ? (dst_tmp ? p.vtmp : p.vout) + off : nullptr;
+#pragma unroll
+  for (int j = 0; j < VT; ++j) {
+    const int e = tid + NT * j;
+    if (e < count) {
+      kdst[out0 + e] = sk[pidx<uint32_t>(e)];
+      if (PAIRS) vdst[out0 + e] = sv[pidx<uint32_t>(e)];
+    }
   }
   finish_item<NT>(p, plan_sh, sid, level);
 }
@@ -513,15 +548,28 @@ __global__ void __launch_bounds__(NT, PAIRS ? 1 : 2) seg_sort_kernel(Params p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ unsigned long long item_sh;
   __shared__ int plan_sh;
+  // The queue's bin boundaries live in shared memory and are read per item:
+  // held in registers for the whole loop they would cost the tile sorts
+  // (at 2 CTAs of 512 threads, 64 registers a thread) registers they need.
+  __shared__ unsigned long long q_sh[5];   // medium, small, tiny, merge, total
+  __shared__ int max_level_sh;
   const int tid = threadIdx.x;
   Ctrl *c = p.ctrl;
-  const unsigned long long q_medium = c->q_medium, q_small = c->q_small, q_tiny = c->q_tiny,
-                           q_merge = c->q_merge, q_total = c->q_total;
-  const int max_level = c->max_level;
+  if (tid == 0) {
+    q_sh[0] = c->q_medium;
+    q_sh[1] = c->q_small;
+    q_sh[2] = c->q_tiny;
+    q_sh[3] = c->q_merge;
+    q_sh[4] = c->q_total;
+    max_level_sh = c->max_level;
+  }
   for (;;) {
     if (tid == 0) item_sh = atomicAdd(&c->next_item, 1ull);
     __syncthreads();
     const unsigned long long item = item_sh;
+    const unsigned long long q_medium = q_sh[0], q_small = q_sh[1], q_tiny = q_sh[2],
+                             q_merge = q_sh[3], q_total = q_sh[4];
+    const int max_level = max_level_sh;
     __syncthreads();
     if (item >= q_total) break;
     if (item < q_medium) {
