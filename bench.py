@@ -296,30 +296,35 @@ def bind_to_gpu_numa_node(torch, dev: int):
         return None
 
 
-def copy_bandwidths(torch, host, dev_a, dev_b):
-    """GB/s of one host-to-device copy of `host` (pinned) into dev_a alone,
-    one device-to-host copy of dev_b alone, and of both at once on two
-    streams."""
+def copy_bandwidths(torch, host, dev_a, dev_b, reps: int = 3):
+    """GB/s of a host-to-device copy of `host` (pinned) into dev_a alone, a
+    device-to-host copy of dev_b alone, and of both at once on two streams:
+    the best of `reps` repeats each (what the link sustains, not one sample
+    that another process on the host happened to slow down)."""
     s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
     back = torch.empty_like(host).pin_memory()
     nbytes = host.numel() * host.element_size()
     res = {}
     for name in ("h2d", "d2h", "both"):
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        a.record(s1)
-        s2.wait_event(a)
-        if name in ("h2d", "both"):
-            with torch.cuda.stream(s1):
-                dev_a.copy_(host, non_blocking=True)
-        if name in ("d2h", "both"):
-            with torch.cuda.stream(s2):
-                back.copy_(dev_b, non_blocking=True)
-        s1.wait_stream(s2)
-        b.record(s1)
-        torch.cuda.synchronize()
-        res[name + "_gbs"] = (2 if name == "both" else 1) * nbytes / (a.elapsed_time(b) / 1e3) / 1e9
+        best = 0.0
+        for _ in range(reps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(s1)
+            s2.wait_event(a)
+            if name in ("h2d", "both"):
+                with torch.cuda.stream(s1):
+                    dev_a.copy_(host, non_blocking=True)
+            if name in ("d2h", "both"):
+                with torch.cuda.stream(s2):
+                    back.copy_(dev_b, non_blocking=True)
+            s1.wait_stream(s2)
+            b.record(s1)
+            torch.cuda.synchronize()
+            gbs = (2 if name == "both" else 1) * nbytes / (a.elapsed_time(b) / 1e3) / 1e9
+            best = max(best, gbs)
+        res[name + "_gbs"] = best
     return res
 
 
@@ -384,16 +389,19 @@ def bench_e2e(nsort, torch, host_in, x, out, tmp, n, code, steps, world, esize=4
     stages = {name: float(np.mean([marks[i][2 * j].elapsed_time(marks[i][2 * j + 1])
                                    for i in range(2, 2 + ke)]))
               for j, name in enumerate(("upload_ms", "sort_ms", "download_ms"))}
-    # one step alone, start to finish (no overlap between steps)
-    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    s0.record(comp)
-    with torch.cuda.stream(comp):
-        din[0].copy_(host_in, non_blocking=True)
-        nsort.nsort_keys(din[0], dout[0], n, code, tmp, tmp.numel(), comp.cuda_stream)
-        hout[0].copy_(dout[0], non_blocking=True)
-    s1.record(comp)
-    torch.cuda.synchronize()
-    serial_ms = s0.elapsed_time(s1)
+    # one step alone, start to finish (no overlap between steps); the best
+    # of three, as for the copy bandwidths
+    serial_ms = float("inf")
+    for _ in range(3):
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(comp)
+        with torch.cuda.stream(comp):
+            din[0].copy_(host_in, non_blocking=True)
+            nsort.nsort_keys(din[0], dout[0], n, code, tmp, tmp.numel(), comp.cuda_stream)
+            hout[0].copy_(dout[0], non_blocking=True)
+        s1.record(comp)
+        torch.cuda.synchronize()
+        serial_ms = min(serial_ms, s0.elapsed_time(s1))
     bw = copy_bandwidths(torch, host_in, din[1], dout[1])
     return {"value": e2e_value, "unit": UNIT, "copy_bandwidths": bw,
             "stages_in_pipeline": stages,
