@@ -230,15 +230,41 @@ def time_oracle(bits: np.ndarray, dtype: str, seconds: float):
     return reps, el
 
 
+def parallel_oracle_rate(x: np.ndarray, dtype: str, threads: int, seconds: float):
+    """Keys/s of the oracle's multi-threaded form on `threads` host threads
+    (32-bit dtypes only)."""
+    import oracle
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        oracle.sort_keys_par(x, dtype, threads)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return reps * x.size / el
+
+
 def cpu_baseline(dtype: str):
     from paper_2409_03970_gb300 import inputs
     n = 1 << CPU_BASELINE_LOG2
     x = sample_keys(n, dtype)
     reps, el = time_oracle(x, dtype, CPU_BASELINE_SECONDS)
-    return {"value": reps * n / el / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+    cores = len(os.sched_getaffinity(0))
+    line = {"value": reps * n / el / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"first 2^{CPU_BASELINE_LOG2} keys of the workload (uniform {dtype}, "
                       f"seed 0), sorted {reps} times in {el:.1f} s by the single-threaded "
-                      f"oracle; host has {len(os.sched_getaffinity(0))} cores"}
+                      f"oracle; host has {cores} cores"}
+    if dtype not in WIDE:
+        # context: the same sort on every host core (chunk sorts, then pairwise
+        # merges); never allowed to break the line
+        try:
+            rate = parallel_oracle_rate(x, dtype, cores, CPU_BASELINE_SECONDS / 2)
+            line["parallel"] = {"value": rate / 1e9, "unit": UNIT, "cores": cores,
+                                "kind": "oracle, multi-threaded: chunk sorts, then pairwise "
+                                        "merges (context, not the baseline)"}
+        except Exception as e:   # noqa: BLE001
+            line["parallel"] = {"error": str(e)[:200]}
+    return line
 
 
 def run_reference(args, rank, world):

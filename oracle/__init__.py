@@ -10,7 +10,9 @@ Two parts:
   method computes — a stable ascending sort of 32-bit keys (paper Sec. 2.1),
   written as a textbook bottom-up merge sort, plus the order-preserving key
   map for int32 / float32 keys (IEEE 754-2008 totalOrder for float32), and
-  the same for 64-bit keys (uint64 / int64 / float64).
+  the same for 64-bit keys (uint64 / int64 / float64).  A multi-threaded
+  form of the same sort (chunk sorts, then pairwise merges) gives the CPU
+  baseline's second figure; the tests check it against the serial one.
 * ``networks.py``: the comparator networks the paper compares in Table 1
   (bitonic, odd-even, the 60-comparator 16-input network) and the merging
   networks of Sec. 2.4, as data, with an exhaustive 0-1-principle verifier.
@@ -45,7 +47,8 @@ def compile_source(src: str, out: str) -> str:
     (plain C, portable: no target-specific flags)."""
     os.makedirs(os.path.dirname(out), exist_ok=True)
     tmp = out + ".%d.tmp" % os.getpid()
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, src])
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-pthread", "-shared", "-fPIC", "-o", tmp,
+                           src])
     os.replace(tmp, out)
     return out
 
@@ -102,6 +105,8 @@ class Oracle:
         lib.orc_key_array.restype = None
         lib.orc_sort_keys.argtypes = [u32p, u32p, ctypes.c_uint64, ctypes.c_int]
         lib.orc_sort_keys.restype = ctypes.c_int
+        lib.orc_sort_keys_par.argtypes = [u32p, u32p, ctypes.c_uint64, ctypes.c_int, ctypes.c_int]
+        lib.orc_sort_keys_par.restype = ctypes.c_int
         lib.orc_sort_pairs.argtypes = [u32p, u32p, u32p, u32p, ctypes.c_uint64, ctypes.c_int]
         lib.orc_sort_pairs.restype = ctypes.c_int
         lib.orc_sort_segmented.argtypes = [u32p, u32p, u32p, u32p, i64p,
@@ -131,6 +136,16 @@ class Oracle:
         rc = self.lib.orc_sort_keys(_p(b), _p(out), b.size, _dt(dtype))
         if rc != 0:
             raise RuntimeError(f"orc_sort_keys failed ({rc})")
+        return out
+
+    def sort_keys_par(self, bits, dtype: str, threads: int) -> np.ndarray:
+        """sort_keys on `threads` host threads (chunk sorts, then pairwise
+        merges): the CPU baseline's multi-threaded figure."""
+        b = _u32(bits)
+        out = np.empty_like(b)
+        rc = self.lib.orc_sort_keys_par(_p(b), _p(out), b.size, _dt(dtype), int(threads))
+        if rc != 0:
+            raise RuntimeError(f"orc_sort_keys_par failed ({rc})")
         return out
 
     def key64(self, bits, dtype: str) -> np.ndarray:
@@ -200,6 +215,10 @@ def key(bits, dtype: str) -> np.ndarray:
 
 def sort_keys(bits, dtype: str) -> np.ndarray:
     return default().sort_keys(bits, dtype)
+
+
+def sort_keys_par(bits, dtype: str, threads: int) -> np.ndarray:
+    return default().sort_keys_par(bits, dtype, threads)
 
 
 def sort_pairs(bits, vals, dtype: str):

@@ -29,6 +29,7 @@
  * table of special values and of the signed-integer order, invariants
  * (non-decreasing, permutation, stability) and closed forms.
  */
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -150,6 +151,114 @@ int orc_sort_pairs(const uint32_t *keys_in, const uint32_t *vals_in,
     if (!vals_in || !vals_out)
         return -1;
     return sort_impl(keys_in, vals_in, keys_out, vals_out, n, dtype);
+}
+
+/* ---- multi-threaded variant, the CPU baseline's second figure ----------
+ * The same sort on `threads` host threads, parallelised the plain way: the
+ * array is cut into `threads` chunks that the threads sort on their own
+ * (sort_impl), then ceil(log2(threads)) rounds merge neighbouring sorted
+ * chunks pairwise (merge_runs, left chunk first on ties), each merge of a
+ * round in its own thread.  A stable merge of stably sorted neighbours is
+ * the stable sort, so the result equals orc_sort_keys; the tests check that. */
+struct par_job {
+    const uint32_t *src;
+    uint32_t *dst;
+    uint64_t lo, mid, hi;
+    int dtype, rc;
+};
+
+static void *par_sort_chunk(void *arg)
+{
+    struct par_job *j = arg;
+    j->rc = sort_impl(j->src + j->lo, NULL, j->dst + j->lo, NULL, j->hi - j->lo, j->dtype);
+    return NULL;
+}
+
+static void *par_merge(void *arg)
+{
+    struct par_job *j = arg;
+    merge_runs(j->src, NULL, j->dst, NULL, j->lo, j->mid, j->hi, j->dtype);
+    j->rc = 0;
+    return NULL;
+}
+
+/* Runs fn on every job, one thread each; returns 0, or -4 when a thread
+ * cannot be started, or the first job's nonzero rc. */
+static int par_run(void *(*fn)(void *), struct par_job *jobs, int count)
+{
+    pthread_t *tid = malloc((size_t)count * sizeof(pthread_t));
+    int started = 0, rc = 0;
+    if (!tid)
+        return -2;
+    for (; started < count; started++)
+        if (pthread_create(&tid[started], NULL, fn, &jobs[started]) != 0) {
+            rc = -4;
+            break;
+        }
+    for (int i = 0; i < started; i++)
+        pthread_join(tid[i], NULL);
+    free(tid);
+    for (int i = 0; rc == 0 && i < started; i++)
+        rc = jobs[i].rc;
+    return rc;
+}
+
+/* Keys only, on `threads` threads (1..256).  Returns 0, -1 on a bad dtype or
+ * thread count, -2 when memory cannot be allocated, -4 when a thread cannot
+ * be started. */
+int orc_sort_keys_par(const uint32_t *keys_in, uint32_t *keys_out, uint64_t n, int dtype,
+                      int threads)
+{
+    if (dtype != ORC_U32 && dtype != ORC_I32 && dtype != ORC_F32)
+        return -1;
+    if (threads < 1 || threads > 256)
+        return -1;
+    if (n == 0)
+        return 0;
+    uint64_t bound[257];
+    for (int i = 0; i <= threads; i++)
+        bound[i] = n * (uint64_t)i / (uint64_t)threads;
+    uint32_t *a = malloc(n * sizeof(uint32_t));
+    uint32_t *b = malloc(n * sizeof(uint32_t));
+    struct par_job *jobs = malloc((size_t)threads * sizeof(struct par_job));
+    int rc = 0;
+    if (!a || !b || !jobs) {
+        rc = -2;
+        goto out;
+    }
+    for (int i = 0; i < threads; i++) {
+        jobs[i].src = keys_in;
+        jobs[i].dst = a;
+        jobs[i].lo = bound[i];
+        jobs[i].hi = bound[i + 1];
+        jobs[i].dtype = dtype;
+    }
+    rc = par_run(par_sort_chunk, jobs, threads);
+    for (int w = 1; rc == 0 && w < threads; w *= 2) {
+        int count = 0;
+        for (int c = 0; c < threads; c += 2 * w) {
+            const int m = c + w < threads ? c + w : threads;
+            const int e = c + 2 * w < threads ? c + 2 * w : threads;
+            jobs[count].src = a;
+            jobs[count].dst = b;
+            jobs[count].lo = bound[c];
+            jobs[count].mid = bound[m];
+            jobs[count].hi = bound[e];
+            jobs[count].dtype = dtype;
+            count++;
+        }
+        rc = par_run(par_merge, jobs, count);
+        uint32_t *t = a;
+        a = b;
+        b = t;
+    }
+    if (rc == 0)
+        memcpy(keys_out, a, n * sizeof(uint32_t));
+out:
+    free(a);
+    free(b);
+    free(jobs);
+    return rc;
 }
 
 /* Segmented: each [offsets[s], offsets[s+1]) is sorted on its own; segments

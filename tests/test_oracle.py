@@ -196,6 +196,28 @@ def test_invariants_all_distributions(dtype, dist):
     np.testing.assert_array_equal(np.sort(y), np.sort(x))      # same multiset of patterns
 
 
+@pytest.mark.parametrize("threads", [1, 2, 3, 8, 16])
+@pytest.mark.parametrize("dist", ["uniform", "dup16", "reverse"])
+def test_multithreaded_oracle_equals_the_serial_one(threads, dist):
+    """The CPU baseline's multi-threaded form (chunk sorts, pairwise merges)
+    returns exactly the serial oracle's result, including ragged chunks and
+    more threads than keys."""
+    for n in (0, 1, 5, 17, 20_011):
+        for dt in ("u32", "i32", "f32"):
+            x = inputs.keys(n, dt, dist, seed=n + threads)
+            np.testing.assert_array_equal(oracle.sort_keys_par(x, dt, threads),
+                                          oracle.sort_keys(x, dt))
+
+
+def test_multithreaded_oracle_rejects_bad_arguments():
+    x = inputs.keys(10, "u32", "uniform", seed=1)
+    for dt, threads in (("u32", 0), ("u32", 257)):
+        with pytest.raises(RuntimeError):
+            oracle.sort_keys_par(x, dt, threads)
+    with pytest.raises(ValueError):
+        oracle.sort_keys_par(x, "u64", 2)
+
+
 def test_pairs_with_ieee_specials_invariants():
     n = 50000
     k, v = inputs.normal_pairs(n, seed=3, special_per_mille=20)
