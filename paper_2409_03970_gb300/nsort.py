@@ -142,10 +142,17 @@ def lib():
 # ---- marshalling ------------------------------------------------------------
 
 def _ptr(x) -> int:
+    """Device address of a buffer argument: None -> 0, an int is taken as a
+    device address as is, a tensor must be a contiguous CUDA tensor (every
+    buffer of the C ABI is a contiguous device array)."""
     if x is None:
         return 0
     if isinstance(x, int):
         return x
+    if not getattr(x, "is_cuda", False):
+        raise ValueError("nsort buffers must be CUDA tensors (or raw device addresses)")
+    if not x.is_contiguous():
+        raise ValueError("nsort buffers must be contiguous")
     return x.data_ptr()
 
 

@@ -87,6 +87,17 @@ def test_argument_validation_needs_no_gpu(lib):
         assert lib.nsort_status_string(s)
 
 
+def test_binding_rejects_host_tensors(lib):
+    """The binding passes device addresses only: a CPU tensor (whose host
+    address a kernel would be handed) is refused before the call."""
+    torch = pytest.importorskip("torch")
+    x = torch.zeros(16, dtype=torch.int32)
+    with pytest.raises(ValueError):
+        nsort.nsort_keys(x, x, 16, nsort.I32, None, 0, 0)
+    with pytest.raises(ValueError):
+        nsort.nsort_pairs(0x1000, x, 0x2000, 0x3000, 16, nsort.I32, None, 0, 0)
+
+
 # ---- column-sort networks of the ablation (include/nsort_ablation.h) ----
 
 FAMILIES = {"bitonic": nsort.NET_BITONIC, "oddeven": nsort.NET_ODDEVEN, "best": nsort.NET_BEST}
