@@ -56,8 +56,8 @@ def parse():
                     default="plain",
                     help="plain: the headline line (with batched/served extras); segmented / "
                          "served: that measurement alone, as its own line")
-    ap.add_argument("--served-duration", type=float, default=10.0,
-                    help="seconds of Poisson arrivals in the served measurement (60 = full)")
+    ap.add_argument("--served-duration", type=float, default=60.0,
+                    help="seconds of Poisson arrivals in the served measurement (60 = the stated workload)")
     ap.add_argument("--segments", type=int, default=100_000)
     ap.add_argument("--no-numa-bind", action="store_true",
                     help="do not restrict the process to the GPU's NUMA node")

@@ -98,6 +98,14 @@ int nsort_plan(int kind, uint64_t n, int *passes, int *sort_tile, int *merge_til
 int nsort_plan_dtype(int kind, uint64_t n, int dtype, int *passes, int *sort_tile,
                      int *merge_tile);
 
+/* CTAs of the persistent merge pass on the current device for `kind`
+ * (KEYS or PAIRS) and `dtype`: SMs x the merge kernel's resident CTAs per
+ * SM.  A merge pass of at most twice that many merge tiles finds its
+ * merge-path splitters inside the merge kernel; a larger pass launches the
+ * partition kernel first (the paper's "segmentation points", Sec. 3.2).
+ * Returns 0 for a bad kind or dtype, or when a CUDA query fails. */
+int nsort_merge_grid(int kind, int dtype);
+
 /* Sorts n keys ascending (paper Sec. 2.1: "the input sequence of the length
  * N").  d_keys_in / d_keys_out: n 32-bit patterns, contiguous, or n 64-bit
  * patterns for the 64-bit dtypes (8-byte aligned; the paper's register
@@ -167,16 +175,29 @@ int nsort_segmented_get_config(nsort_seg_config *cfg);
  *  - n up to NSORT_NOALLOC_MAX_KEYS; larger n returns NSORT_ENOMEM with an
  *    explanation in nsort_last_error().  Other errors as nsort_keys.
  *  - Calls nothing that allocates (no cudaMalloc / cudaFree).
+ *  - The array used is the one of the CURRENT device; `stream` must belong
+ *    to that device.
  *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress, with that device current); make that first call
- *    before any stream capture.
+ *    (cudaGetSymbolAddress, with that device current) and keeps it for the
+ *    life of the process; make that first call before any stream capture.
+ *    The kept address does not survive cudaDeviceReset: do not call these
+ *    entry points again in a process that has reset the device.
  *  - All calls on a device share the one array, which keeps whatever the last
- *    call left in it (nothing in it needs to start at zero).  Calls whose
+ *    call left in it.  Each call clears the status word (below) on its
+ *    stream; nothing else in it needs to start at zero.  Calls whose
  *    work overlaps on the GPU race on it: issue them on one stream, or order
  *    them with events. */
 #define NSORT_NOALLOC_MAX_KEYS (1u << 20)
 int nsort_keys_noalloc(const void *d_keys_in, void *d_keys_out, uint64_t n, int dtype,
                        void *stream);
+
+/* Device status of the last nsort_keys_noalloc on the current device, read
+ * in order on `stream` (it synchronises that stream): NSORT_OK, or
+ * NSORT_ETIMEOUT when a bounded wait inside a merge pass gave up and that
+ * call's output is incomplete (this does not happen in normal operation).
+ * It plays the part nsort_device_status plays for calls given a scratch
+ * buffer.  NSORT_ECUDA if the read fails.  Allocates nothing. */
+int nsort_keys_noalloc_status(void *stream);
 
 /* ---- serving: continuous batching of sort requests --------------------
  * A context owns a scheduler thread, a pool of CUDA streams and a device

@@ -12,7 +12,10 @@
 // Host code cannot use the array's name as a device address (on the host it
 // names a stand-in), so the device address is looked up with
 // cudaGetSymbolAddress once per device, with that device current, the first
-// time the entry point runs on it.
+// time the entry point runs on it.  The address is kept for the life of the
+// process: it does not survive cudaDeviceReset (or any other end of the
+// device's primary context), after which these entry points must not be
+// called again in the process.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -94,9 +97,32 @@ extern "C" int nsort_keys_noalloc(const void *d_keys_in, void *d_keys_out, uint6
   void *scratch = nullptr;
   const int rc = scratch_for_current_device(&scratch);
   if (rc != NSORT_OK) return rc;
-  // Nothing in the scratch has to start at zero: the tile sort writes the
-  // whole key buffer and every pass writes its splitters before reading them.
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // The status word (the array's first bytes) starts every call at
+  // NSORT_OK, also for sorts without merge passes, which never write it:
+  // nsort_keys_noalloc_status then always reports this call.  Nothing else
+  // in the scratch has to start at zero: the tile sort writes the whole key
+  // buffer and every pass writes its splitters before reading them.
+  if (cudaMemsetAsync(scratch, 0, sizeof(int), st) != cudaSuccess) {
+    set_last_error(std::string("nsort_keys_noalloc: cudaMemsetAsync: ") +
+                   cudaGetErrorString(cudaGetLastError()));
+    return NSORT_ECUDA;
+  }
   return sort_keys_impl(static_cast<const uint32_t *>(d_keys_in),
-                        static_cast<uint32_t *>(d_keys_out), (int64_t)n, dtype, scratch,
-                        static_cast<cudaStream_t>(stream));
+                        static_cast<uint32_t *>(d_keys_out), (int64_t)n, dtype, scratch, st);
+}
+
+extern "C" int nsort_keys_noalloc_status(void *stream) {
+  void *scratch = nullptr;
+  const int rc = scratch_for_current_device(&scratch);
+  if (rc != NSORT_OK) return rc;
+  int status = 0;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (cudaMemcpyAsync(&status, scratch, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    set_last_error(std::string("nsort_keys_noalloc_status: ") +
+                   cudaGetErrorString(cudaGetLastError()));
+    return NSORT_ECUDA;
+  }
+  return status;
 }

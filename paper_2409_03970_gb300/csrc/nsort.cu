@@ -1301,6 +1301,14 @@ extern "C" int nsort_plan_dtype(int kind, uint64_t n, int dtype, int *passes, in
   return NSORT_OK;
 }
 
+extern "C" int nsort_merge_grid(int kind, int dtype) {
+  if (kind != NSORT_KIND_KEYS && kind != NSORT_KIND_PAIRS) return 0;
+  if (is_wide(dtype) && kind != NSORT_KIND_KEYS) return 0;
+  const int which = kind == NSORT_KIND_PAIRS ? 1 : (is_wide(dtype) ? 2 : 0);
+  const int g = tma_merge_grid(INT64_MAX, which);
+  return cudaGetLastError() == cudaSuccess ? g : 0;
+}
+
 extern "C" int nsort_plan(int kind, uint64_t n, int *passes, int *sort_tile, int *merge_tile) {
   return nsort_plan_dtype(kind, n, NSORT_U32, passes, sort_tile, merge_tile);
 }

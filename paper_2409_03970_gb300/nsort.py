@@ -81,6 +81,8 @@ def _load():
         lib.nsort_plan.restype = i32
         lib.nsort_plan_dtype.argtypes = [i32, u64, i32, ip, ip, ip]
         lib.nsort_plan_dtype.restype = i32
+        lib.nsort_merge_grid.argtypes = [i32, i32]
+        lib.nsort_merge_grid.restype = i32
         lib.nsort_keys.argtypes = [vp, vp, u64, i32, vp, sz, vp]
         lib.nsort_keys.restype = i32
         lib.nsort_pairs.argtypes = [vp, vp, vp, vp, u64, i32, vp, sz, vp]
@@ -113,6 +115,8 @@ def _load():
         lib.nsort_selftest_wait.restype = i32
         lib.nsort_keys_noalloc.argtypes = [vp, vp, u64, i32, vp]
         lib.nsort_keys_noalloc.restype = i32
+        lib.nsort_keys_noalloc_status.argtypes = [vp]
+        lib.nsort_keys_noalloc_status.restype = i32
         i32p = ctypes.POINTER(ctypes.c_int32)
         lib.nsort_network.argtypes = [i32, i32, i32p, i32p, i32]
         lib.nsort_network.restype = i32
@@ -188,6 +192,11 @@ def _check_1d(t, name):
 
 def nsort_temp_bytes(kind: int, n: int, nseg: int = 0, dtype: int = U32) -> int:
     return int(_load().nsort_temp_bytes(kind, n, nseg, dtype))
+
+
+def nsort_merge_grid(kind: int, dtype: int = U32) -> int:
+    """CTAs of the persistent merge pass on the current device (0 on error)."""
+    return int(_load().nsort_merge_grid(kind, dtype))
 
 
 def nsort_plan(kind: int, n: int, dtype: int = U32):
@@ -350,6 +359,12 @@ def nsort_keys_noalloc(keys_in, keys_out, n: int, dtype: int, stream=None) -> in
     allocate device memory (scratch is a fixed array inside the library;
     n <= NOALLOC_MAX_KEYS; calls that overlap on the GPU race on it)."""
     return _load().nsort_keys_noalloc(_ptr(keys_in), _ptr(keys_out), n, dtype, _stream(stream))
+
+
+def nsort_keys_noalloc_status(stream=None) -> int:
+    """Device status of the last nsort_keys_noalloc on the current device
+    (synchronises `stream`)."""
+    return _load().nsort_keys_noalloc_status(_stream(stream))
 
 
 class TraceEntry(ctypes.Structure):

@@ -152,11 +152,13 @@ def test_zero_one_principle_8_input_network_on_gpu(ns):
 
 
 def test_cuda_graph_capture_and_replay(ns):
+    """One nsort_segmented captured into a CUDA graph, replayed on new keys
+    copied into the captured input buffer before each replay: every replay
+    sorts the data it finds there."""
     ns.nsort_segmented_set_config()
     off = mixed_offsets(6)
     n, nseg = int(off[-1]), off.size - 1
-    x = inputs.keys(n, "u32", "uniform", seed=6)
-    kt, ot = dev(x), dev(off, np.int64)
+    kt, ot = dev(inputs.keys(n, "u32", "uniform", seed=6)), dev(off, np.int64)
     ko = torch.empty_like(kt)
     tmp = ns.scratch(ns.KIND_SEGMENTED, n, nseg)
     s = torch.cuda.Stream()
@@ -167,19 +169,63 @@ def test_cuda_graph_capture_and_replay(ns):
     with torch.cuda.graph(g, stream=s):
         rc = ns.nsort_segmented(kt, ko, None, None, ot, nseg, n, 0, tmp, tmp.numel(), s)
     assert rc == ns.OK
-    want = oracle.sort_segmented(x, off, "u32")
-    for seed in (7, 8):
+    for seed, dist in ((7, "uniform"), (8, "dup16"), (9, "reverse")):
+        x = inputs.keys(n, "u32", dist, seed=seed)
+        kt.copy_(dev(x))
         ko.zero_()
+        torch.cuda.synchronize()
         g.replay()
         torch.cuda.synchronize()
-        np.testing.assert_array_equal(ko.cpu().numpy().view(np.uint32), want)
+        np.testing.assert_array_equal(ko.cpu().numpy().view(np.uint32),
+                                      oracle.sort_segmented(x, off, "u32"))
         assert ns.nsort_device_status(tmp) == ns.OK
 
 
 def test_batch_of_the_benchmark_shape(ns):
     """2,000 log-uniform segments of 1..65536 keys (the shape of the
-    100,000-segment benchmark, scaled down for the oracle)."""
+    100,000-segment benchmark, at a size the serial oracle sorts in a
+    second)."""
     ns.nsort_segmented_set_config()
     off = inputs.segment_offsets(2000, seed=9)
     x = inputs.keys(int(off[-1]), "u32", "uniform", seed=9)
     np.testing.assert_array_equal(run_seg(ns, x, off, "u32"), oracle.sort_segmented(x, off, "u32"))
+
+
+def oracle_segmented_threaded(x, off, dt):
+    """oracle.sort_segmented applied to contiguous groups of whole segments
+    on all host cores.  Segments are sorted independently, so sorting each
+    group on its own (offsets rebased to the group) is the same computation
+    as one call over the batch."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+    try:
+        threads = max(1, len(os.sched_getaffinity(0)))
+    except AttributeError:
+        threads = max(1, os.cpu_count() or 1)
+    n, nseg = int(off[-1]), off.size - 1
+    cuts = np.searchsorted(off, np.linspace(0, n, threads + 1)[1:-1])
+    bounds = [0] + sorted(set(int(c) for c in cuts if 0 < c < nseg)) + [nseg]
+    out = np.empty_like(x)
+
+    def run(i):
+        s0, s1 = bounds[i], bounds[i + 1]
+        k0, k1 = int(off[s0]), int(off[s1])
+        out[k0:k1] = oracle.sort_segmented(x[k0:k1], off[s0:s1 + 1] - k0, dt)
+
+    with ThreadPoolExecutor(threads) as ex:
+        list(ex.map(run, range(len(bounds) - 1)))
+    return out
+
+
+def test_full_benchmark_batch_against_oracle(ns):
+    """The batched benchmark workload at its full size: 100,000 log-uniform
+    segments of 1..65536 uniform u32 keys (about 5.9e8 keys), in one
+    persistent launch with the default tuning, compared element by element
+    with the oracle."""
+    ns.nsort_segmented_set_config()
+    off = inputs.segment_offsets(100_000, seed=0)
+    x = inputs.keys(int(off[-1]), "u32", "uniform", seed=0)
+    got = run_seg(ns, x, off, "u32")
+    torch.cuda.empty_cache()
+    want = oracle_segmented_threaded(x, off, "u32")
+    assert np.array_equal(got, want)

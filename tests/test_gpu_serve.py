@@ -115,3 +115,19 @@ def test_error_paths(ns):
         assert srv.wait(12345, 10) == ns.ENOTFOUND
         t = srv.submit(x[:0], x[:0])                        # n = 0 completes at once
         assert srv.poll(t)[0]
+
+
+def test_admitted_requests_overlap_and_match_alone(ns):
+    """Continuous batching admits a request while others are on the GPU:
+    two large requests on different stream slots, submitted back to back,
+    are both admitted before either completes (their admit-to-done
+    intervals overlap), and each result equals the oracle's."""
+    n = 1 << 26
+    reqs = [("keys", "u32", inputs.keys(n, "u32", "uniform", seed=31), None),
+            ("keys", "f32", inputs.keys(n, "f32", "zipf", seed=32), None)]
+    budget = 2 * ns.nsort_temp_bytes(ns.KIND_KEYS, n) + (1 << 20)
+    outs, tm = run_all(ns, reqs, streams=2, batch_max_keys=0, budget=budget)
+    assert not any(t["batched"] for t in tm)
+    assert max(t["t_admit"] for t in tm) < min(t["t_done"] for t in tm)
+    for (kind, dt, k, v), (ko, _) in zip(reqs, outs):
+        np.testing.assert_array_equal(ko, oracle.sort_keys(k, dt))

@@ -71,24 +71,35 @@ def test_keys_all_dtypes_distributions(ns, dt, dist, n):
     np.testing.assert_array_equal(gpu_sort(ns, x, dt), oracle.sort_keys(x, dt))
 
 
-# Where the merge passes find their splitters: the persistent merge grid has
-# 152 SMs x 4 CTAs = 608 CTAs on GB300.  Passes with at most one tile per CTA
-# (keys: 608 x 3968 = 2,412,544 keys) or two (4,825,088) find their own
-# splitters inside the merge kernel; larger passes launch the partition
-# kernel.  The sizes straddle both boundaries.
-MODE_SIZES_KEYS = [2_412_544, 2_412_545, 3_000_017, 4_825_088, 4_825_089, 5_000_011]
-MODE_SIZES_PAIRS = [1_167_360, 1_167_361, 2_334_720, 2_334_721]
+# Where the merge passes find their splitters: a pass with at most one or
+# two merge tiles per CTA of the persistent merge grid (SMs x resident CTAs,
+# from nsort_merge_grid on this device) finds its own splitters inside the
+# merge kernel; larger passes launch the partition kernel.  The last pass
+# has about n / merge_tile tiles, so these sizes straddle both boundaries on
+# whatever device runs the tests.
+MODE_POINTS = ["1x", "1x+1", "1.5x", "2x", "2x+1", "2.1x"]
+
+
+def mode_size(ns, kind, dtype, point):
+    grid = ns.nsort_merge_grid(kind, dtype)
+    assert grid > 0, ns.lib().nsort_last_error()
+    tile = ns.nsort_plan(kind, 1 << 24, dtype)[2]
+    one, two = grid * tile, 2 * grid * tile
+    return {"1x": one, "1x+1": one + 1, "1.5x": (one + two) // 2 + 17, "2x": two,
+            "2x+1": two + 1, "2.1x": two + two // 20 + 11}[point]
 
 
 @pytest.mark.parametrize("dist", ["uniform", "sorted", "dup16"])
-@pytest.mark.parametrize("n", MODE_SIZES_KEYS)
-def test_keys_splitter_modes(ns, n, dist):
+@pytest.mark.parametrize("point", MODE_POINTS)
+def test_keys_splitter_modes(ns, point, dist):
+    n = mode_size(ns, ns.KIND_KEYS, ns.U32, point)
     x = inputs.keys(n, "f32", dist, seed=n)
     np.testing.assert_array_equal(gpu_sort(ns, x, "f32"), oracle.sort_keys(x, "f32"))
 
 
-@pytest.mark.parametrize("n", MODE_SIZES_PAIRS)
-def test_pairs_splitter_modes(ns, n):
+@pytest.mark.parametrize("point", ["1x", "1x+1", "2x", "2x+1"])
+def test_pairs_splitter_modes(ns, point):
+    n = mode_size(ns, ns.KIND_PAIRS, ns.U32, point)
     k = inputs.keys(n, "i32", "dup16", seed=n)
     v = inputs.counter_u32(5, 6, 0, n)
     ko, vo = gpu_pairs(ns, k, v, "i32")
@@ -178,47 +189,30 @@ def test_full_size_u32_uniform_against_oracle(ns):
     assert np.array_equal(got, want)
 
 
-def _key_i64(t, dt):
-    """Order key of int32 tensor patterns, as non-negative int64 (test-side)."""
-    if dt == "u32":
-        return t.to(torch.int64) & 0xFFFFFFFF
-    if dt == "i32":
-        return t.to(torch.int64) + (1 << 31)
-    m = (t >> 31) | torch.tensor(-(1 << 31), dtype=torch.int32, device=t.device)
-    return (t ^ m).to(torch.int64) & 0xFFFFFFFF
+def host_threads():
+    """Host cores this process may run on (the oracle's multi-threaded form
+    uses all of them)."""
+    import os
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except AttributeError:
+        return max(1, os.cpu_count() or 1)
 
 
 @pytest.mark.parametrize("dt", ["i32", "f32"])
 @pytest.mark.parametrize("dist", list(inputs.DISTRIBUTIONS))
-def test_full_size_properties(ns, dt, dist):
-    """2^28 keys of each dtype and distribution: the output is non-decreasing
-    in key order; it is a permutation of the input (a 2^16-bucket histogram
-    of the keys and a 64-bit multiset hash agree); and sampled output
-    positions hold the right order statistics (for out[i] = v: fewer than
-    i+1 input keys are below v and more than i are at most v)."""
+def test_full_size_against_oracle(ns, dt, dist):
+    """The 2^28-key workloads of each dtype and distribution, in the launch
+    configuration the benchmark times, compared element by element with the
+    oracle (its multi-threaded form, which equals the serial sort: the
+    oracle's own tests check that)."""
     n = 1 << 28
     x = inputs.keys(n, dt, dist, seed=2)
-    xt = dev(x)
+    got = gpu_sort(ns, x, dt)
+    torch.cuda.empty_cache()
+    want = oracle.sort_keys_par(x, dt, host_threads())
     del x
-    out = torch.empty_like(xt)
-    tmp = ns.scratch(ns.KIND_KEYS, n)
-    assert ns.nsort_keys(xt, out, n, DT[dt], tmp, tmp.numel()) == ns.OK
-    del tmp
-    k = _key_i64(out, dt)
-    assert bool((k[1:] >= k[:-1]).all())
-    ki = _key_i64(xt, dt)
-    h_in = torch.bincount((ki >> 16), minlength=1 << 16)
-    h_out = torch.bincount((k >> 16), minlength=1 << 16)
-    assert torch.equal(h_in, h_out)
-    c1, c2 = 0x9E3779B97F4A7C15 - (1 << 64), 0xBF58476D1CE4E5B9 - (1 << 64)
-    mix = lambda z: ((z * c1) ^ (z >> 29)) * c2          # int64, wraps mod 2^64
-    assert int(mix(ki).sum()) == int(mix(k).sum())
-    # patterns, not just keys: the key map is a bijection, so equal keys are equal patterns
-    assert int(xt.to(torch.int64).sum()) == int(out.to(torch.int64).sum())
-    for i in inputs.counter_u64(9, 0, 0, 12) % np.uint64(n):
-        i = int(i)
-        v = k[i]
-        assert int((ki < v).sum()) <= i < int((ki <= v).sum())
+    assert np.array_equal(got, want)
 
 
 def test_full_size_pairs_against_oracle(ns):

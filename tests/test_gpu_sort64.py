@@ -77,11 +77,16 @@ def test_keys64_f64_totalorder_table(ns, golden):
     assert first == sorted(first)
 
 
-@pytest.mark.parametrize("n", [1_167_360, 1_167_361, 2_334_720, 2_334_721])
-def test_keys64_splitter_modes(ns, n):
+@pytest.mark.parametrize("point", [1, 2])
+@pytest.mark.parametrize("extra", [0, 1])
+def test_keys64_splitter_modes(ns, point, extra):
     """Sizes at the boundaries between merge passes that find their own
-    splitters (at most one, or two, 1920-key tiles per CTA of the 608-CTA
-    grid) and passes that launch the partition kernel."""
+    splitters (at most one, or two, merge tiles per CTA of the persistent
+    merge grid on this device) and passes that launch the partition kernel."""
+    grid = ns.nsort_merge_grid(ns.KIND_KEYS, DT["i64"])
+    assert grid > 0
+    tile = ns.nsort_plan(ns.KIND_KEYS, 1 << 24, DT["i64"])[2]
+    n = point * grid * tile + extra
     x = inputs.keys64(n, "i64", "dup16", seed=n)
     assert np.array_equal(gpu_sort64(ns, x, "i64"), oracle.sort_keys64(x, "i64"))
 
