@@ -65,7 +65,9 @@ typedef enum {
     NSORT_KIND_KEYS = 0,            /* nsort_keys */
     NSORT_KIND_PAIRS = 1,           /* nsort_pairs */
     NSORT_KIND_SEGMENTED = 2,       /* nsort_segmented, keys only */
-    NSORT_KIND_SEGMENTED_PAIRS = 3  /* nsort_segmented with values */
+    NSORT_KIND_SEGMENTED_PAIRS = 3, /* nsort_segmented with values */
+    NSORT_KIND_MERGE = 4,           /* nsort_merge_shards, keys only (nseg = number of runs) */
+    NSORT_KIND_MERGE_PAIRS = 5      /* nsort_merge_shards with values */
 } nsort_kind;
 
 typedef enum {
@@ -150,6 +152,65 @@ int nsort_segmented(const void *d_keys_in, void *d_keys_out,
                     const uint32_t *d_vals_in, uint32_t *d_vals_out,
                     const int64_t *d_offsets, uint64_t nseg, uint64_t n, int dtype,
                     void *d_tmp, size_t tmp_bytes, void *stream);
+
+/* ---- sharded sort: one array split over P workers ----------------------
+ * The paper's parallel merge (Sec. 2.1, last paragraph; Sec. 3.2): P
+ * workers each sort a part, the output is partitioned evenly at
+ * "segmentation points" (how many keys of each part precede each output
+ * position), and each worker merges the slices that fall in its share.
+ * With one worker per GPU: each GPU sorts its shard (nsort_keys /
+ * nsort_pairs), the splitters come from nsort_count_le summed over the
+ * GPUs (or, with every shard in one buffer, from nsort_shard_coranks), the
+ * slices are exchanged (an all-to-all), and each GPU merges what it
+ * received with nsort_merge_shards.  The result is the stable sort of the
+ * concatenated shards: ascending key order, equal keys in shard order, then
+ * in their order within the shard. */
+
+/* Segmentation points of P sorted shards stored back to back in one device
+ * buffer (shard r = keys [d_shard_off[r], d_shard_off[r+1]); d_shard_off is
+ * a DEVICE array of nshards+1 int64, non-decreasing, nshards 1..32; each
+ * shard sorted ascending in the key order of dtype).  For each of the
+ * ntargets output positions d = d_targets[j] (DEVICE int64, clamped to
+ * [0, total keys]) of the stable merge of the shards, writes to
+ * d_coranks[j * nshards + r] (DEVICE int64) how many of the first d outputs
+ * come from shard r; these sum to d.  Exact for any data, ties included
+ * (equal keys go to the lower shard first).  One warp per target, bisection
+ * on the order-key space (32 rounds, 64 for the 64-bit dtypes).  Errors:
+ * NSORT_EINVAL (bad dtype, shard count, NULL or misaligned pointer),
+ * NSORT_ECUDA.  Allocates nothing. */
+int nsort_shard_coranks(const void *d_keys, const int64_t *d_shard_off, int nshards,
+                        const int64_t *d_targets, int ntargets, int dtype,
+                        int64_t *d_coranks, void *stream);
+
+/* The per-GPU step of the same splitter search across GPUs: for a sorted
+ * array of n keys (key order of dtype) and m bounds given as ORDER keys
+ * (d_bounds: uint32, or uint64 for the 64-bit dtypes: the order-preserving
+ * map's unsigned keys, 0 = the smallest key of the dtype), writes
+ * d_le[i] = the number of keys whose order key is <= d_bounds[i] (DEVICE
+ * int64).  A caller bisects each splitter's key on the sum of these counts
+ * over the GPUs (one all-reduce per round), as nsort_shard_coranks does in
+ * one kernel.  Errors: NSORT_EINVAL, NSORT_ECUDA.  Allocates nothing. */
+int nsort_count_le(const void *d_sorted, uint64_t n, int dtype, const void *d_bounds,
+                   uint64_t m, int64_t *d_le, void *stream);
+
+/* Merges nruns sorted runs stored back to back into one sorted array: a
+ * worker's merge of the slices it received (paper Sec. 2.1, last
+ * paragraph).  h_run_off: HOST array of nruns+1 int64, run r =
+ * [h_run_off[r], h_run_off[r+1]), h_run_off[0] == 0, non-decreasing,
+ * h_run_off[nruns] = n; nruns 1..64; empty runs allowed.  Each run sorted
+ * ascending in the key order of dtype (as nsort_keys / nsort_pairs leave
+ * it).  Stable: equal keys keep run order, then position.  d_vals_in /
+ * d_vals_out: 32-bit payloads moved with their keys, or both NULL (keys
+ * only; the 64-bit dtypes are keys only).  All buffers 16-byte aligned;
+ * the output must not overlap the input.  Runs in ceil(log2(nruns))
+ * two-way merge passes.  Scratch: nsort_temp_bytes(NSORT_KIND_MERGE[_PAIRS],
+ * n, nruns, dtype), 256-byte aligned (0 bytes for one run).  Errors:
+ * NSORT_EINVAL (offsets, dtype, pointers, alignment, overlap), NSORT_ENOMEM
+ * (scratch too small), NSORT_ECUDA.  If a run is not sorted the output is
+ * unspecified, but every access stays inside the buffers. */
+int nsort_merge_shards(const void *d_keys_in, const uint32_t *d_vals_in, void *d_keys_out,
+                       uint32_t *d_vals_out, const int64_t *h_run_off, int nruns, int dtype,
+                       void *d_tmp, size_t tmp_bytes, void *stream);
 
 /* Tunables of nsort_segmented, set by the autotuner (process-wide). */
 typedef struct {

@@ -367,19 +367,73 @@ struct PairTile {
   int na, nb, count;
 };
 
+// Where tile t of a merge pass lies: the first element of its pair of runs
+// (run A, then run B, back to back), the two run lengths, and the tile's
+// index within the pair.
+struct PairSpan {
+  int64_t pair0, la, lb, j;
+};
+
+// The runs of one pass of a sort: n elements in runs of `run` (the last ones
+// shorter); pair p owns tpp = ceil(2 run / tile) consecutive tiles.  Keys
+// are order keys in and out (the kernel's DT_OUT maps them back).
+struct UniformRuns {
+  static constexpr bool kMaps = false;
+  int64_t n, run, tpp;
+  int dt_in = DT_U32, dt_out = DT_U32;   // unused
+  __device__ __forceinline__ PairSpan span(int64_t t) const {
+    PairSpan s;
+    const int64_t pair = t / tpp;
+    s.j = t - pair * tpp;
+    s.pair0 = pair * 2 * run;
+    s.la = n - s.pair0 < run ? n - s.pair0 : run;
+    const int64_t rest = n - s.pair0 - run;
+    s.lb = rest <= 0 ? 0 : (rest < run ? rest : run);
+    return s;
+  }
+};
+
+// Runs of any lengths, back to back (the merge of sorted shards): pair p
+// is runs 2p and 2p+1 (B empty for an odd last run) and owns the tiles
+// [first_tile[p], first_tile[p+1]).  Passed by value as a kernel argument.
+// The keys arrive as bit patterns of dtype dt_in (DT_U32 / DT_U64: order
+// keys already) and leave mapped back to dt_out, chosen at run time: a
+// merge of shards runs a few passes, so one kernel serves every dtype.
+constexpr int MAX_TABLE_PAIRS = 32;
+struct TableRuns {
+  static constexpr bool kMaps = true;
+  int dt_in, dt_out;
+  int npairs;
+  int64_t first_tile[MAX_TABLE_PAIRS + 1];
+  int64_t pair0[MAX_TABLE_PAIRS];
+  int64_t la[MAX_TABLE_PAIRS];
+  int64_t lb[MAX_TABLE_PAIRS];
+  __device__ __forceinline__ PairSpan span(int64_t t) const {
+    int lo = 0, hi = npairs - 1;   // the last pair p with first_tile[p] <= t (skips empty pairs)
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (first_tile[mid] <= t) lo = mid;
+      else hi = mid - 1;
+    }
+    PairSpan s;
+    s.pair0 = pair0[lo];
+    s.la = la[lo];
+    s.lb = lb[lo];
+    s.j = t - first_tile[lo];
+    return s;
+  }
+};
+
 // Geometry of tile t from its start splitter s0 and the next tile's s1
 // (s1 is ignored when the tile ends its pair).
-__device__ __forceinline__ PairTile pair_tile_from(int64_t t, int64_t n, int64_t run, int64_t tpp,
-                                                   int tile, int64_t s0, int64_t s1) {
+template <class GEOM>
+__device__ __forceinline__ PairTile pair_tile_from(int64_t t, const GEOM &geom, int tile,
+                                                   int64_t s0, int64_t s1) {
   PairTile g;
-  const int64_t pair = t / tpp;
-  const int64_t j = t - pair * tpp;
-  const int64_t pair0 = pair * 2 * run;
-  const int64_t la = n - pair0 < run ? n - pair0 : run;
-  const int64_t rest = n - pair0 - run;
-  const int64_t lb = rest <= 0 ? 0 : (rest < run ? rest : run);
+  const PairSpan sp = geom.span(t);
+  const int64_t pair0 = sp.pair0, la = sp.la, lb = sp.lb;
   const int64_t pend = pair0 + la + lb;
-  g.out0 = pair0 + j * tile;
+  g.out0 = pair0 + sp.j * tile;
   const int64_t out1 = g.out0 + tile < pend ? g.out0 + tile : pend;
   int64_t a0 = s0;
   int64_t a1 = out1 == pend ? la : s1;
@@ -394,33 +448,36 @@ __device__ __forceinline__ PairTile pair_tile_from(int64_t t, int64_t n, int64_t
 
 // Splitter of tile v of the pair-aligned tiling (what the partition kernels
 // write to split[v]), found by a group of W lanes of one warp.
-template <int W, typename K>
-__device__ __forceinline__ int64_t tile_corank_group(const K *src, int64_t n, int64_t run,
-                                                     int64_t tpp, int tile, int64_t v, int glane,
-                                                     unsigned gmask) {
-  const int64_t pair = v / tpp;
-  const int64_t j = v - pair * tpp;
-  const int64_t pair0 = pair * 2 * run;
-  const int64_t la = n - pair0 < run ? n - pair0 : run;
-  const int64_t rest = n - pair0 - run;
-  const int64_t lb = rest <= 0 ? 0 : (rest < run ? rest : run);
-  return merge_path_global_group<W>(src + pair0, la, src + pair0 + la, lb, j * tile, glane, gmask);
+template <int W, typename K, class GEOM>
+__device__ __forceinline__ int64_t tile_corank_group(const K *src, const GEOM &geom, int tile,
+                                                     int64_t v, int glane, unsigned gmask) {
+  const PairSpan sp = geom.span(v);
+  return merge_path_global_group<W>(src + sp.pair0, sp.la, src + sp.pair0 + sp.la, sp.lb,
+                                    sp.j * tile, glane, gmask);
 }
 
-// Splitters for the pair-aligned tiling, one thread per tile.
-__global__ void partition_pairs_kernel(const uint32_t *__restrict__ src, int64_t n, int64_t run,
-                                       int64_t tpp, int tile, int64_t num_tiles,
-                                       int64_t *__restrict__ split) {
+// Splitters for the pair-aligned tiling, one thread per tile, by a full
+// merge-path search.  The keys are compared as order keys: a geometry that
+// maps (the first pass over bit patterns) maps every key it loads.
+template <typename K, class GEOM>
+__global__ void partition_pairs_kernel(const K *__restrict__ src, const GEOM geom, int tile,
+                                       int64_t num_tiles, int64_t *__restrict__ split) {
   pdl_wait();      // the previous kernel of the stream has finished writing
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= num_tiles) return;
-  const int64_t pair = t / tpp;
-  const int64_t j = t - pair * tpp;
-  const int64_t pair0 = pair * 2 * run;
-  const int64_t la = n - pair0 < run ? n - pair0 : run;
-  const int64_t rest = n - pair0 - run;
-  const int64_t lb = rest <= 0 ? 0 : (rest < run ? rest : run);
-  split[t] = merge_path_global(src + pair0, la, src + pair0 + la, lb, j * tile);
+  const PairSpan sp = geom.span(t);
+  const int dt = GEOM::kMaps ? geom.dt_in : DT_U32;
+  const K *A = src + sp.pair0;
+  const K *B = A + sp.la;
+  const int64_t d = sp.j * tile;
+  int64_t lo = d - sp.lb > 0 ? d - sp.lb : 0;
+  int64_t hi = d < sp.la ? d : sp.la;
+  while (lo < hi) {   // A's share of the first d outputs (A first on ties)
+    const int64_t mid = (lo + hi) >> 1;
+    if (to_key(__ldg(A + mid), dt) <= to_key(__ldg(B + (d - 1 - mid)), dt)) lo = mid + 1;
+    else hi = mid;
+  }
+  split[t] = lo;
 }
 
 // Sampled partition for the pair-aligned tiling.  SA / SB are the samples
@@ -542,14 +599,22 @@ __device__ __forceinline__ void issue_tile(const K *__restrict__ src,
 // too small to hide them: the first tile's start and end (lanes 0-15 and
 // 16-31 at once, 16-ary searches) before its copies are issued, then the
 // second tile's while those copies land.
-template <int NT, int VT, int DT_OUT, bool PAIRS, typename K = uint32_t, bool SELF = false>
+// GEOM: where each tile's runs lie (UniformRuns for the passes of a sort,
+// TableRuns for merging runs of any lengths; the latter also maps keys from
+// bit patterns on arrival and back on the way out, by its run-time dtypes,
+// in place of DT_OUT).
+template <int NT, int VT, int DT_OUT, bool PAIRS, typename K = uint32_t, bool SELF = false,
+          class GEOM = UniformRuns>
 __global__ void __launch_bounds__(NT, PAIRS ? 3 : 4) merge_tma_kernel(
     const K *__restrict__ src, const uint32_t *__restrict__ vsrc, K *__restrict__ dst,
-    uint32_t *__restrict__ vdst, int64_t n, int64_t run, int64_t tpp, int64_t num_tiles,
+    uint32_t *__restrict__ vdst, int64_t n, const GEOM geom, int64_t num_tiles,
     const int64_t *__restrict__ split, int *status, K *samp, int reverse) {
   pdl_wait();      // the previous kernel of the stream has finished writing
   constexpr int TILE = NT * VT;
   constexpr int WOUT = 32 * VT;                       // outputs per warp
+  // staging stride per warp: a table of runs can start a warp's outputs
+  // anywhere, so its staging is shifted to the output's 16-byte phase
+  constexpr int WSTRIDE = WOUT + (GEOM::kMaps ? 16 / (int)sizeof(K) : 0);
   constexpr int EPV = 16 / sizeof(K);                 // keys per 16 bytes
   // A window + gap, B window + gap, rounding slack
   constexpr int IN_LEN = (TILE + 2 * SENT + 16) & ~3;
@@ -565,7 +630,7 @@ __global__ void __launch_bounds__(NT, PAIRS ? 3 : 4) merge_tma_kernel(
       tma_smem + (PAIRS ? 2 * IN_LEN * sizeof(K) : 0));
   K *out_buf = reinterpret_cast<K *>(tma_smem + (PAIRS ? 2 * IN_LEN * (sizeof(K) + 4)
                                                         : 2 * IN_LEN * sizeof(K)));
-  uint32_t *vout_buf = reinterpret_cast<uint32_t *>(out_buf + TILE);
+  uint32_t *vout_buf = reinterpret_cast<uint32_t *>(out_buf + (NT / 32) * WSTRIDE);
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ PairTile desc[2];   // geometry of the tile in each buffer, written by thread 0
   const int tid = threadIdx.x;
@@ -586,7 +651,7 @@ __global__ void __launch_bounds__(NT, PAIRS ? 3 : 4) merge_tma_kernel(
     const int64_t v = tile_of(i) + (lane >> 4);
     const unsigned gmask = 0xFFFFu << (lane & 16);
     int64_t c = 0;
-    if (v < num_tiles) c = tile_corank_group<16>(src, n, run, tpp, TILE, v, lane & 15, gmask);
+    if (v < num_tiles) c = tile_corank_group<16>(src, geom, TILE, v, lane & 15, gmask);
     s1 = __shfl_sync(0xffffffffu, c, 16);
     s0 = c;
   };
@@ -600,10 +665,9 @@ __global__ void __launch_bounds__(NT, PAIRS ? 3 : 4) merge_tma_kernel(
     if (t < num_tiles) {
       const int64_t u = tile_of(t);
       if constexpr (SELF)
-        desc[0] = pair_tile_from(u, n, run, tpp, TILE, own0, own1);
+        desc[0] = pair_tile_from(u, geom, TILE, own0, own1);
       else
-        desc[0] = pair_tile_from(u, n, run, tpp, TILE, split[u],
-                                 u + 1 < num_tiles ? split[u + 1] : 0);
+        desc[0] = pair_tile_from(u, geom, TILE, split[u], u + 1 < num_tiles ? split[u + 1] : 0);
       issue_tile(src, PAIRS ? vsrc : nullptr, n_al, desc[0], in_buf[0], vin_buf[0], &bar[0]);
     }
     if constexpr (!SELF) {
@@ -619,8 +683,8 @@ __global__ void __launch_bounds__(NT, PAIRS ? 3 : 4) merge_tma_kernel(
   }
   __syncthreads();
   bool ok = true;
-  K *wout = out_buf + warp * WOUT;
-  uint32_t *wvout = vout_buf + warp * WOUT;
+  K *wout = out_buf + warp * WSTRIDE;
+  uint32_t *wvout = vout_buf + warp * WSTRIDE;
   for (int it = 0; t < num_tiles; ++it, t += G) {
     const int b = it & 1;
     const int64_t tn = t + G;
@@ -635,7 +699,7 @@ __global__ void __launch_bounds__(NT, PAIRS ? 3 : 4) merge_tma_kernel(
     }
     // every thread is past the previous tile: its buffer and descriptor are free
     if (tid == 0 && tn < num_tiles) {
-      desc[b ^ 1] = pair_tile_from(tile_of(tn), n, run, tpp, TILE, pf0, pf1);
+      desc[b ^ 1] = pair_tile_from(tile_of(tn), geom, TILE, pf0, pf1);
       issue_tile(src, PAIRS ? vsrc : nullptr, n_al, desc[b ^ 1], in_buf[b ^ 1], vin_buf[b ^ 1],
                  &bar[b ^ 1]);
       if constexpr (!SELF) {   // (a self-partitioned pass has at most two tiles per CTA)
@@ -652,19 +716,31 @@ __global__ void __launch_bounds__(NT, PAIRS ? 3 : 4) merge_tma_kernel(
     K *s = in_buf[b];
     uint32_t *sv = vin_buf[b];
     const int a0 = l.sh_a, b0 = l.base_b + l.sh_b;
+    if constexpr (GEOM::kMaps) {
+      if (geom.dt_in != DT_U32 && geom.dt_in != DT_U64) {   // the same in every thread
+        // bit patterns in: map the bulk-copied part of both slices to order
+        // keys in place, all threads, before any warp reads them
+        const int64_t ca = n_al - g.a_off, cb = n_al - g.b_off;
+        const int na_cp = ca <= 0 ? 0 : (ca < g.na ? (int)ca : g.na);
+        const int nb_cp = cb <= 0 ? 0 : (cb < g.nb ? (int)cb : g.nb);
+        for (int i = tid; i < na_cp; i += NT) s[a0 + i] = to_key(s[a0 + i], geom.dt_in);
+        for (int i = tid; i < nb_cp; i += NT) s[b0 + i] = to_key(s[b0 + i], geom.dt_in);
+        __syncthreads();
+      }
+    }
     // this warp's own array-end elements (and sentinels, for keys); the same
     // values in every warp
     if (g.a_off + g.na > n_al || g.b_off + g.nb > n_al) {
       if (lane < EPV - 1) {
         const int64_t i = (g.a_off > n_al ? g.a_off : n_al) + lane;
         if (i < g.a_off + g.na) {
-          s[a0 + (int)(i - g.a_off)] = __ldg(src + i);
+          s[a0 + (int)(i - g.a_off)] = to_key(__ldg(src + i), GEOM::kMaps ? geom.dt_in : DT_U32);
           if (PAIRS) sv[a0 + (int)(i - g.a_off)] = __ldg(vsrc + i);
         }
       } else if (lane < 2 * (EPV - 1)) {
         const int64_t i = (g.b_off > n_al ? g.b_off : n_al) + (lane - (EPV - 1));
         if (i < g.b_off + g.nb) {
-          s[b0 + (int)(i - g.b_off)] = __ldg(src + i);
+          s[b0 + (int)(i - g.b_off)] = to_key(__ldg(src + i), GEOM::kMaps ? geom.dt_in : DT_U32);
           if (PAIRS) sv[b0 + (int)(i - g.b_off)] = __ldg(vsrc + i);
         }
       }
@@ -689,40 +765,56 @@ __global__ void __launch_bounds__(NT, PAIRS ? 3 : 4) merge_tma_kernel(
     // this warp's slice of the output: stage, then one bulk store per array
     const int w0 = warp * WOUT;
     const int wcount = g.count - w0 < WOUT ? g.count - w0 : WOUT;
+    const int64_t gb = g.out0 + w0;                  // the warp's first output
+    // sh: gb's offset past a 16-byte boundary, 0 for the uniform runs of a sort
+    const int sh = GEOM::kMaps ? (int)(gb & (EPV - 1)) : 0;
+    K *ws = wout + sh;
+    uint32_t *wvs = wvout + sh;
     if (lane == 0) bulk_wait_read_all();   // the warp's previous stores have left its slices
     __syncwarp();
+    const int dt_out = GEOM::kMaps ? geom.dt_out : DT_OUT;   // a constant unless GEOM maps
     if (g.count == TILE) {
 #pragma unroll
       for (int k = 0; k < VT; ++k) {
-        wout[lane * VT + k] = from_key(o[k], DT_OUT);
-        if (PAIRS) wvout[lane * VT + k] = ov[k];
+        ws[lane * VT + k] = from_key(o[k], dt_out);
+        if (PAIRS) wvs[lane * VT + k] = ov[k];
       }
     } else {
 #pragma unroll
       for (int k = 0; k < VT; ++k) {
         if (tid * VT + k < g.count) {
-          wout[lane * VT + k] = from_key(o[k], DT_OUT);
-          if (PAIRS) wvout[lane * VT + k] = ov[k];
+          ws[lane * VT + k] = from_key(o[k], dt_out);
+          if (PAIRS) wvs[lane * VT + k] = ov[k];
         }
       }
     }
     fence_proxy_async_smem();
     __syncwarp();
     if (samp && wcount > 0) {   // every SAMPLE-th output key, for the next partition
-      const int64_t gb = g.out0 + w0;
       const int e = (int)((SAMPLE - (gb & (SAMPLE - 1))) & (SAMPLE - 1)) + SAMPLE * lane;
-      if (e < wcount) store_keep_in_l2(samp + (gb + e) / SAMPLE, wout[e]);
+      if (e < wcount) store_keep_in_l2(samp + (gb + e) / SAMPLE, ws[e]);
     }
     if (wcount > 0) {
-      const int body = wcount & ~(EPV - 1);
+      // head: plain stores up to the first 16-byte boundary (none when sh =
+      // 0); body: one bulk store per array (smem and global addresses both
+      // 16-byte aligned, since ws and dst + gb share their phase); tail:
+      // plain stores of the last EPV - 1 or fewer
+      const int hd = (EPV - sh) & (EPV - 1);
+      const int head = hd < wcount ? hd : wcount;
+      const int body = (wcount - head) & ~(EPV - 1);
+      const int tail = wcount - head - body;
       if (lane == 0 && body) {
-        bulk_store(dst + g.out0 + w0, wout, (uint32_t)body * (uint32_t)sizeof(K));
-        if (PAIRS) bulk_store(vdst + g.out0 + w0, wvout, (uint32_t)body * 4u);
+        bulk_store(dst + gb + head, ws + head, (uint32_t)body * (uint32_t)sizeof(K));
+        if (PAIRS) bulk_store(vdst + gb + head, wvs + head, (uint32_t)body * 4u);
         bulk_commit();
       }
-      if (lane < (wcount & (EPV - 1))) {
-        dst[g.out0 + w0 + body + lane] = wout[body + lane];
-        if (PAIRS) vdst[g.out0 + w0 + body + lane] = wvout[body + lane];
+      if (lane < head) {
+        dst[gb + lane] = ws[lane];
+        if (PAIRS) vdst[gb + lane] = wvs[lane];
+      }
+      if (lane < tail) {
+        dst[gb + head + body + lane] = ws[head + body + lane];
+        if (PAIRS) vdst[gb + head + body + lane] = wvs[head + body + lane];
       }
     }
   }
@@ -1049,6 +1141,7 @@ static void launch_merge_tma(const uint32_t *src, const uint32_t *vsrc, uint32_t
   int64_t tpp = 0;
   const int64_t tiles = pair_tiles(n, run, tile, &tpp);
   const unsigned grid = (unsigned)tma_merge_grid(tiles, pairs ? 1 : 0);
+  const UniformRuns geom{n, run, tpp};
   if (tiles > 2 * (int64_t)grid) {
     TraceScope tr(TK_PARTITION, st);
     launch_pdl(partition_sampled_kernel<uint32_t>, (unsigned)((tiles + 255) / 256), 256, 0, st,
@@ -1059,7 +1152,7 @@ static void launch_merge_tma(const uint32_t *src, const uint32_t *vsrc, uint32_t
   TraceScope tr(pairs ? TK_MERGE_PAIRS : TK_MERGE_KEYS, st);
 #define NSORT_MT1(NT, VT, DT, P, SMEM, SELF)                                                   \
   launch_pdl(merge_tma_kernel<NT, VT, DT, P, uint32_t, SELF>, grid, NT, SMEM, st, src, vsrc, dst, \
-             vdst, n, run, tpp, tiles, split, status, samp_out, reverse)
+             vdst, n, geom, tiles, split, status, samp_out, reverse)
 #define NSORT_MT(NT, VT, DT, P, SMEM)                                                        \
   do {                                                                                       \
     if (split) NSORT_MT1(NT, VT, DT, P, SMEM, false);                                       \
@@ -1101,6 +1194,7 @@ static void launch_merge_tma64(const uint64_t *src, uint64_t *dst, int64_t n, in
   int64_t tpp = 0;
   const int64_t tiles = pair_tiles(n, run, TMA_K64_TILE, &tpp);
   const unsigned grid = (unsigned)tma_merge_grid(tiles, 2);
+  const UniformRuns geom{n, run, tpp};
   if (tiles > 2 * (int64_t)grid) {
     TraceScope tr(TK_PARTITION, st);
     launch_pdl(partition_sampled_kernel<uint64_t>, (unsigned)((tiles + 255) / 256), 256, 0, st,
@@ -1113,7 +1207,7 @@ static void launch_merge_tma64(const uint64_t *src, uint64_t *dst, int64_t n, in
   uint32_t *no_vals_out = nullptr;
 #define NSORT_MT64S(DT, SELF)                                                                \
   launch_pdl(merge_tma_kernel<TMA_K64_NT, TMA_K64_VT, DT, false, uint64_t, SELF>, grid,       \
-             TMA_K64_NT, TMA_K64_SMEM, st, src, no_vals, dst, no_vals_out, n, run, tpp, tiles, \
+             TMA_K64_NT, TMA_K64_SMEM, st, src, no_vals, dst, no_vals_out, n, geom, tiles, \
              split, status, samp_out, reverse)
 #define NSORT_MT64(DT)                                                                       \
   do {                                                                                       \
@@ -1273,6 +1367,162 @@ int sort_pairs_impl(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, ui
   return rc;
 }
 
+// ---- merging sorted runs of any lengths (the local merge of a sharded sort)
+//
+// A tree of two-way passes: pass 1 merges runs (0,1), (2,3), ...; each pass
+// halves the number of runs (an odd last run is copied through as a merge
+// with an empty partner).  Every pass is the persistent bulk-copy merge
+// kernel with a table of the pass's run pairs (TableRuns); ties take the
+// earlier run, so the merge is stable by run, then by position.  The first
+// pass maps the bit patterns to order keys as they arrive and the last one
+// maps them back.  Buffers ping-pong between the output and the scratch so
+// that the last pass lands in the output.
+
+size_t merge_runs_temp_bytes(bool pairs, uint64_t n, uint64_t nruns, int dtype) {
+  if (nruns < 2) return 0;
+  const bool wide = !pairs && dtype >= NSORT_U64;
+  const size_t kw = wide ? 8 : 4;
+  const int tile = pairs ? TMA_PMERGE_TILE : (wide ? TMA_K64_TILE : TMA_MERGE_TILE);
+  const size_t tiles = (size_t)(n / (uint64_t)tile) + (size_t)nruns + 2;
+  size_t total = 256;                                        // status word
+  total += align_up((size_t)n * kw, 256);                    // ping-pong keys
+  if (pairs) total += align_up((size_t)n * 4, 256);          // ping-pong values
+  total += align_up(tiles * sizeof(int64_t), 256);           // splitters
+  return total;
+}
+
+// Fills the run-pair table of one pass over runs with boundaries off[0..nr]
+// and returns its number of tiles.
+static int64_t fill_run_table(const int64_t *off, int nr, int tile, int dt_in, int dt_out,
+                              TableRuns &tab) {
+  tab.dt_in = dt_in;
+  tab.dt_out = dt_out;
+  tab.npairs = (nr + 1) / 2;
+  int64_t tiles = 0;
+  for (int p = 0; p < tab.npairs; ++p) {
+    const int64_t a = off[2 * p];
+    const int64_t m = off[2 * p + 1 < nr ? 2 * p + 1 : nr];
+    const int64_t e = off[2 * p + 2 < nr ? 2 * p + 2 : nr];
+    tab.pair0[p] = a;
+    tab.la[p] = m - a;
+    tab.lb[p] = e - m;
+    tab.first_tile[p] = tiles;
+    tiles += (e - a + tile - 1) / tile;
+  }
+  tab.first_tile[tab.npairs] = tiles;
+  return tiles;
+}
+
+template <typename K, bool PAIRS>
+static void table_merge_attrs(const void *fn, size_t smem) {
+  static std::atomic<uint64_t> done_mask{0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const uint64_t bit = dev < 64 ? (uint64_t(1) << dev) : 0;
+  if (bit && (done_mask.load() & bit)) return;
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  done_mask.fetch_or(bit);
+}
+
+// One pass over a table of run pairs: the partition (one splitter per tile,
+// a full merge-path search each), then the persistent merge.
+template <typename K, bool PAIRS>
+static void launch_table_pass(const K *src, const uint32_t *vsrc, K *dst, uint32_t *vdst,
+                              int64_t n, const TableRuns &tab, int64_t tiles, int64_t *split,
+                              int *status, cudaStream_t st) {
+  constexpr bool WIDE = sizeof(K) == 8;
+  constexpr int NT = PAIRS ? TMA_PMERGE_NT : (WIDE ? TMA_K64_NT : TMA_MERGE_NT);
+  constexpr int VT = PAIRS ? TMA_PMERGE_VT : (WIDE ? TMA_K64_VT : TMA_MERGE_VT);
+  constexpr int TILE = NT * VT;
+  // the uniform-run kernel's shared memory plus the shifted staging: 16
+  // bytes per warp and output array
+  constexpr size_t SMEM = (PAIRS ? TMA_PMERGE_SMEM : (WIDE ? TMA_K64_SMEM : TMA_MERGE_SMEM)) +
+                          (size_t)(NT / 32) * 16 * (PAIRS ? 2 : 1);
+  constexpr int DT0 = WIDE ? DT_U64 : DT_U32;   // unused: TableRuns maps at run time
+  auto kernel = merge_tma_kernel<NT, VT, DT0, PAIRS, K, false, TableRuns>;
+  table_merge_attrs<K, PAIRS>((const void *)kernel, SMEM);
+  const unsigned grid = (unsigned)tma_merge_grid(tiles, PAIRS ? 1 : (WIDE ? 2 : 0));
+  {
+    TraceScope tr(TK_PARTITION, st);
+    launch_pdl(partition_pairs_kernel<K, TableRuns>, (unsigned)((tiles + 255) / 256), 256, 0, st,
+               src, tab, TILE, tiles, split);
+  }
+  TraceScope tr(PAIRS ? TK_MERGE_PAIRS : (WIDE ? TK_MERGE_KEYS64 : TK_MERGE_KEYS), st);
+  K *no_samples = nullptr;
+  launch_pdl(kernel, grid, NT, SMEM, st, src, vsrc, dst, vdst, n, tab, tiles,
+             (const int64_t *)split, status, no_samples, 0);
+}
+
+template <typename K, bool PAIRS>
+static int merge_runs_typed(const K *kin, const uint32_t *vin, K *kout, uint32_t *vout,
+                            const int64_t *off, int nruns, int dt, void *tmp, cudaStream_t st) {
+  constexpr bool WIDE = sizeof(K) == 8;
+  constexpr int TILE = PAIRS ? TMA_PMERGE_TILE : (WIDE ? TMA_K64_TILE : TMA_MERGE_TILE);
+  const int64_t n = off[nruns];
+  int passes = 0;
+  while ((1 << passes) < nruns) ++passes;
+  if (passes == 0) {   // one run: already sorted
+    if (n > 0 && kout != kin &&
+        cudaMemcpyAsync(kout, kin, (size_t)n * sizeof(K), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      return launch_status("cudaMemcpyAsync");
+    if (PAIRS && n > 0 && vout != vin &&
+        cudaMemcpyAsync(vout, vin, (size_t)n * 4, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      return launch_status("cudaMemcpyAsync");
+    return NSORT_OK;
+  }
+  char *t = static_cast<char *>(tmp);
+  int *status = reinterpret_cast<int *>(t);
+  K *ktmp = reinterpret_cast<K *>(t + 256);
+  const size_t kb = align_up((size_t)n * sizeof(K), 256);
+  uint32_t *vtmp = PAIRS ? reinterpret_cast<uint32_t *>(t + 256 + kb) : nullptr;
+  int64_t *split = reinterpret_cast<int64_t *>(t + 256 + kb + (PAIRS ? align_up((size_t)n * 4, 256) : 0));
+  if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess)
+    return launch_status("cudaMemsetAsync");
+  int64_t cur_off[2 * MAX_TABLE_PAIRS + 1];
+  int nr = nruns;
+  for (int r = 0; r <= nr; ++r) cur_off[r] = off[r];
+  const K *src = kin;
+  const uint32_t *vsrc = vin;
+  const int order = WIDE ? DT_U64 : DT_U32;   // order keys between passes
+  int rc = NSORT_OK;
+  for (int pass = 0; rc == NSORT_OK && pass < passes; ++pass) {
+    const bool last = pass == passes - 1;
+    const bool to_out = ((passes - 1 - pass) & 1) == 0;
+    K *dst = to_out ? kout : ktmp;
+    uint32_t *vdst = PAIRS ? (to_out ? vout : vtmp) : nullptr;
+    TableRuns tab;
+    const int64_t tiles = fill_run_table(cur_off, nr, TILE, pass == 0 ? dt : order,
+                                         last ? dt : order, tab);
+    if (tiles > 0)
+      launch_table_pass<K, PAIRS>(src, vsrc, dst, vdst, n, tab, tiles, split, status, st);
+    rc = launch_status("merge_shards");
+    // the merged pairs are the next pass's runs
+    int m = 0;
+    for (int r = 0; r < nr; r += 2) cur_off[m++] = cur_off[r];
+    cur_off[m] = cur_off[nr];
+    nr = m;
+    src = dst;
+    vsrc = vdst;
+  }
+  return rc;
+}
+
+int merge_runs_impl(const void *kin, const uint32_t *vin, void *kout, uint32_t *vout,
+                    const int64_t *off, int nruns, int dt, void *tmp, cudaStream_t st) {
+  if (vin)
+    return merge_runs_typed<uint32_t, true>(static_cast<const uint32_t *>(kin), vin,
+                                            static_cast<uint32_t *>(kout), vout, off, nruns, dt,
+                                            tmp, st);
+  if (dt >= NSORT_U64)
+    return merge_runs_typed<uint64_t, false>(static_cast<const uint64_t *>(kin), nullptr,
+                                             static_cast<uint64_t *>(kout), nullptr, off, nruns,
+                                             dt, tmp, st);
+  return merge_runs_typed<uint32_t, false>(static_cast<const uint32_t *>(kin), nullptr,
+                                           static_cast<uint32_t *>(kout), nullptr, off, nruns, dt,
+                                           tmp, st);
+}
+
 }  // namespace nsort
 
 // ---------------------------------------------------------------- C ABI
@@ -1286,6 +1536,8 @@ static bool is_wide(int dtype) {
 extern "C" size_t nsort_temp_bytes(int kind, uint64_t n, uint64_t nseg, int dtype) {
   if (kind == NSORT_KIND_KEYS) return make_plan(kind, n, is_wide(dtype) ? dtype : 0).total;
   if (kind == NSORT_KIND_PAIRS) return make_plan(kind, n).total;
+  if (kind == NSORT_KIND_MERGE) return merge_runs_temp_bytes(false, n, nseg, dtype);
+  if (kind == NSORT_KIND_MERGE_PAIRS) return merge_runs_temp_bytes(true, n, nseg, dtype);
   return segmented_temp_bytes(kind, n, nseg);
 }
 
@@ -1356,6 +1608,44 @@ extern "C" int nsort_pairs(const void *d_keys_in, const uint32_t *d_vals_in, voi
     return NSORT_EINVAL;
   return sort_pairs_impl(static_cast<const uint32_t *>(d_keys_in), d_vals_in,
                          static_cast<uint32_t *>(d_keys_out), d_vals_out, (int64_t)n, dtype,
+                         d_tmp, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int nsort_merge_shards(const void *d_keys_in, const uint32_t *d_vals_in,
+                                  void *d_keys_out, uint32_t *d_vals_out, const int64_t *h_run_off,
+                                  int nruns, int dtype, void *d_tmp, size_t tmp_bytes,
+                                  void *stream) {
+  const bool pairs = d_vals_in != nullptr || d_vals_out != nullptr;
+  const bool wide = is_wide(dtype);
+  if (dtype < NSORT_U32 || dtype > NSORT_F64 || (pairs && wide)) return NSORT_EINVAL;
+  if (!h_run_off || nruns < 1 || nruns > 2 * MAX_TABLE_PAIRS) return NSORT_EINVAL;
+  if (h_run_off[0] != 0) return NSORT_EINVAL;
+  for (int r = 0; r < nruns; ++r)
+    if (h_run_off[r + 1] < h_run_off[r]) return NSORT_EINVAL;
+  const int64_t n = h_run_off[nruns];
+  if ((uint64_t)n > MAX_KEYS) return NSORT_EINVAL;
+  if (n == 0) return NSORT_OK;
+  if (!d_keys_in || !d_keys_out || (pairs && (!d_vals_in || !d_vals_out))) return NSORT_EINVAL;
+  const uintptr_t bufs = reinterpret_cast<uintptr_t>(d_keys_in) |
+                         reinterpret_cast<uintptr_t>(d_keys_out) |
+                         reinterpret_cast<uintptr_t>(d_vals_in) |
+                         reinterpret_cast<uintptr_t>(d_vals_out);
+  if (bufs & 15) return NSORT_EINVAL;   // the passes stage their slices with bulk copies
+  if (nruns > 1) {
+    const size_t kw = wide ? 8 : 4;
+    const char *ki = static_cast<const char *>(d_keys_in);
+    const char *ko = static_cast<const char *>(d_keys_out);
+    if (ki < ko + (size_t)n * kw && ko < ki + (size_t)n * kw) return NSORT_EINVAL;
+    if (pairs) {
+      const char *vi = reinterpret_cast<const char *>(d_vals_in);
+      const char *vo = reinterpret_cast<const char *>(d_vals_out);
+      if (vi < vo + (size_t)n * 4 && vo < vi + (size_t)n * 4) return NSORT_EINVAL;
+    }
+    const size_t need = merge_runs_temp_bytes(pairs, (uint64_t)n, (uint64_t)nruns, dtype);
+    if (!d_tmp || tmp_bytes < need) return NSORT_ENOMEM;
+    if (reinterpret_cast<uintptr_t>(d_tmp) & 255) return NSORT_EINVAL;
+  }
+  return merge_runs_impl(d_keys_in, d_vals_in, d_keys_out, d_vals_out, h_run_off, nruns, dtype,
                          d_tmp, static_cast<cudaStream_t>(stream));
 }
 

@@ -41,6 +41,11 @@ int sort_pairs_impl(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, ui
 
 size_t segmented_temp_bytes(int kind, uint64_t n, uint64_t nseg);
 
+// Merge of sorted runs of any lengths (nsort_merge_shards).
+size_t merge_runs_temp_bytes(bool pairs, uint64_t n, uint64_t nruns, int dtype);
+int merge_runs_impl(const void *kin, const uint32_t *vin, void *kout, uint32_t *vout,
+                    const int64_t *off, int nruns, int dt, void *tmp, cudaStream_t st);
+
 // Kernel ids of the tracer (order of its name table).
 enum TraceKernel {
   TK_TILE_SORT_KEYS = 0, TK_TILE_SORT_PAIRS, TK_PARTITION, TK_MERGE_KEYS, TK_MERGE_PAIRS,

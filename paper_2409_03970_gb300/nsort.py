@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libnsort.so")
 U32, I32, F32 = 0, 1, 2
 U64, I64, F64 = 3, 4, 5           # 64-bit keys (nsort_keys only)
 KIND_KEYS, KIND_PAIRS, KIND_SEGMENTED, KIND_SEGMENTED_PAIRS = 0, 1, 2, 3
+KIND_MERGE, KIND_MERGE_PAIRS = 4, 5
 OK, EINVAL, ENOMEM, ECUDA, EBUSY, ETIMEOUT, ENOTFOUND = range(7)
 NET_BITONIC, NET_ODDEVEN, NET_BEST = 0, 1, 2     # include/nsort_ablation.h
 MERGE_HYBRID, MERGE_SHUFFLE, MERGE_SERIAL = 0, 1, 2
@@ -81,6 +82,13 @@ def _load():
         lib.nsort_plan.restype = i32
         lib.nsort_plan_dtype.argtypes = [i32, u64, i32, ip, ip, ip]
         lib.nsort_plan_dtype.restype = i32
+        i64p_ = ctypes.POINTER(ctypes.c_int64)
+        lib.nsort_shard_coranks.argtypes = [vp, vp, i32, vp, i32, i32, vp, vp]
+        lib.nsort_shard_coranks.restype = i32
+        lib.nsort_count_le.argtypes = [vp, u64, i32, vp, u64, vp, vp]
+        lib.nsort_count_le.restype = i32
+        lib.nsort_merge_shards.argtypes = [vp, vp, vp, vp, i64p_, i32, i32, vp, sz, vp]
+        lib.nsort_merge_shards.restype = i32
         lib.nsort_merge_grid.argtypes = [i32, i32]
         lib.nsort_merge_grid.restype = i32
         lib.nsort_keys.argtypes = [vp, vp, u64, i32, vp, sz, vp]
@@ -225,6 +233,32 @@ def nsort_segmented(keys_in, keys_out, vals_in, vals_out, offsets, nseg: int, n:
     return _load().nsort_segmented(_ptr(keys_in), _ptr(keys_out), _ptr(vals_in), _ptr(vals_out),
                                    _ptr(offsets), nseg, n, dtype, _ptr(tmp), tmp_bytes,
                                    _stream(stream))
+
+
+def nsort_shard_coranks(keys, shard_off, nshards: int, targets, ntargets: int, dtype: int,
+                        coranks, stream=None) -> int:
+    """Segmentation points of nshards sorted shards in one device buffer
+    (shard_off, targets, coranks: device int64 arrays)."""
+    return _load().nsort_shard_coranks(_ptr(keys), _ptr(shard_off), nshards, _ptr(targets),
+                                       ntargets, dtype, _ptr(coranks), _stream(stream))
+
+
+def nsort_count_le(sorted_keys, n: int, dtype: int, bounds, m: int, le, stream=None) -> int:
+    """le[i] = keys of the sorted array whose order key is <= bounds[i]
+    (bounds: device uint32 / uint64 order keys; le: device int64)."""
+    return _load().nsort_count_le(_ptr(sorted_keys), n, dtype, _ptr(bounds), m, _ptr(le),
+                                  _stream(stream))
+
+
+def nsort_merge_shards(keys_in, vals_in, keys_out, vals_out, run_off, dtype: int, tmp,
+                       tmp_bytes: int, stream=None) -> int:
+    """Merges sorted runs stored back to back; run_off: the nruns+1 host
+    offsets (any integer sequence)."""
+    offs = [int(x) for x in run_off]
+    arr = (ctypes.c_int64 * len(offs))(*offs)
+    return _load().nsort_merge_shards(_ptr(keys_in), _ptr(vals_in), _ptr(keys_out),
+                                      _ptr(vals_out), arr, len(offs) - 1, dtype, _ptr(tmp),
+                                      tmp_bytes, _stream(stream))
 
 
 def nsort_device_status(tmp, stream=None) -> int:
