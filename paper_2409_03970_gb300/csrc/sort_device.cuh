@@ -327,20 +327,28 @@ __device__ __forceinline__ void serial_merge_plain(const K *s, int a, int a_end,
 // Once a run is exhausted its head reads as the largest key, so the other
 // run is taken; when both heads are the largest key, either may be output —
 // keys only, so equal keys are the same bits and the outputs are exact.
+// The loop keeps the head and index of the run whose head is smaller (lo)
+// and of the other run (hi): each output is lo's head; lo's next key is
+// compared with hi's head once, and four selects set the new (lo, hi).
+// That is one compare and four selects per output, against one compare and
+// seven selects and adds when the two runs keep fixed roles.
 template <int VT, typename K>
 __device__ __forceinline__ void serial_merge_sentinel(const K *s, int a, int b, K (&out)[VT]) {
   K ka = s[a];
   K kb = s[b];
+  const bool t0 = ka <= kb;
+  K hlo = t0 ? ka : kb, hhi = t0 ? kb : ka;
+  int ilo = t0 ? a : b, ihi = t0 ? b : a;
 #pragma unroll
   for (int k = 0; k < VT; ++k) {
-    const bool take_a = ka <= kb;
-    out[k] = take_a ? ka : kb;
-    const int nx = (take_a ? a : b) + 1;
-    const K kn = s[nx];
-    a = take_a ? nx : a;
-    b = take_a ? b : nx;
-    ka = take_a ? kn : ka;
-    kb = take_a ? kb : kn;
+    out[k] = hlo;
+    const int i = ilo + 1;
+    const K kn = s[i];
+    const bool p = kn <= hhi;
+    hlo = p ? kn : hhi;
+    ilo = p ? i : ihi;
+    hhi = p ? hhi : kn;
+    ihi = p ? ihi : i;
   }
 }
 
@@ -387,14 +395,20 @@ struct Green16Columns {
 // elements past a run's end.  Valid for keys only and for the pairs'
 // distinct (key, position) composites: a largest key taken from a gap
 // instead of a real one has the same bits, and no composite is all ones.
-template <int IPT>
-__host__ __device__ constexpr int block_gap() { return IPT + 1; }
+// The gap is IPT + 1 rounded up to whole pad blocks (32 elements for 32-bit
+// keys, 16 for 64-bit ones), so that every run, and every thread's IPT
+// outputs, start at a multiple of IPT within a pad block: a thread's outputs
+// then sit at consecutive padded indices.
+template <typename K>
+__host__ __device__ constexpr int block_gap(int ipt) {
+  return (ipt + 1 + (1 << Pad<K>::SHIFT) - 1) >> Pad<K>::SHIFT << Pad<K>::SHIFT;
+}
 
 // Elements of the block merges' buffer: the tile and one gap per run of the
 // first level (runs of 32 IPT), padded.
 template <typename K>
 __host__ __device__ constexpr int block_smem_len(int nt, int ipt) {
-  return padded_len<K>(nt * ipt + (nt / 32) * (ipt + 1));
+  return padded_len<K>(nt * ipt + (nt / 32) * block_gap<K>(ipt));
 }
 
 // Thread t's IPT consecutive outputs [e0, e0 + IPT), part of a run of R
@@ -402,10 +416,12 @@ __host__ __device__ constexpr int block_smem_len(int nt, int ipt) {
 // warp whose outputs end a run fills that run's gap, a slot or two a lane.
 template <int IPT, typename K>
 __device__ __forceinline__ void stage_gapped(const K (&r)[IPT], K *s, int e0, int run) {
-  constexpr int GAP = block_gap<IPT>();
+  constexpr int GAP = block_gap<K>(IPT);
+  static_assert(((1 << Pad<K>::SHIFT) % IPT) == 0, "a thread's outputs stay in one pad block");
   const int base = e0 + (e0 / run) * GAP;
+  const int pb = pidx<K>(base);   // base's pad block holds all IPT outputs
 #pragma unroll
-  for (int k = 0; k < IPT; ++k) s[pidx<K>(base + k)] = r[k];
+  for (int k = 0; k < IPT; ++k) s[pb + k] = r[k];
   const int lane = threadIdx.x & 31;
   const int wend = e0 + (32 - lane) * IPT;   // end of the warp's outputs (same in every lane)
   if (wend % run == 0) {
@@ -416,21 +432,24 @@ __device__ __forceinline__ void stage_gapped(const K (&r)[IPT], K *s, int e0, in
 
 // Unchecked serial merge on the padded layout: VT outputs of the merge of
 // the runs at element indices a and b, each followed by at least VT + 1
-// largest keys.
+// largest keys.  The same (lo, hi) formulation as serial_merge_sentinel.
 template <int VT, typename K>
 __device__ __forceinline__ void serial_merge_gapped(const K *s, int a, int b, K (&out)[VT]) {
   K ka = s[pidx<K>(a)];
   K kb = s[pidx<K>(b)];
+  const bool t0 = ka <= kb;
+  K hlo = t0 ? ka : kb, hhi = t0 ? kb : ka;
+  int ilo = t0 ? a : b, ihi = t0 ? b : a;
 #pragma unroll
   for (int k = 0; k < VT; ++k) {
-    const bool take_a = ka <= kb;
-    out[k] = take_a ? ka : kb;
-    const int nx = (take_a ? a : b) + 1;
-    const K kn = s[pidx<K>(nx)];
-    a = take_a ? nx : a;
-    b = take_a ? b : nx;
-    ka = take_a ? kn : ka;
-    kb = take_a ? kb : kn;
+    out[k] = hlo;
+    const int i = ilo + 1;
+    const K kn = s[pidx<K>(i)];
+    const bool p = kn <= hhi;
+    hlo = p ? kn : hhi;
+    ilo = p ? i : ihi;
+    hhi = p ? hhi : kn;
+    ihi = p ? ihi : i;
   }
 }
 
@@ -448,7 +467,7 @@ __device__ __forceinline__ void serial_merge_gapped(const K *s, int a, int b, K 
 template <int NT, int IPT, class COLS, typename K, bool GAPPED = true>
 __device__ __forceinline__ void sort_tile_in_block(K (&r)[IPT], K *s) {
   constexpr int TILE = NT * IPT;
-  constexpr int GAP = block_gap<IPT>();
+  constexpr int GAP = block_gap<K>(IPT);
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   COLS::sort(r);
