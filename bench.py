@@ -675,7 +675,7 @@ def bench_batched(nsort, torch, nseg: int, reps: int = 5):
             "batched_gkeys_s": total / ms_b / 1e6, "batched_ms": ms_b,
             "plain_per_array_gkeys_s": total / min(ms_p) / 1e6, "plain_per_array_ms": min(ms_p),
             "speedup": min(ms_p) / ms_b, "identical_results": same,
-            "launch": "one graph-captured nsort_segmented (3 set-up kernels + 1 persistent)",
+            "launch": "one graph-captured nsort_segmented: 3 set-up kernels, 1 persistent kernel (level-0 tiles and short segments), then 3 kernels per merge level (tile list, partition, persistent bulk-copy merge)",
             "autotuned_config": tune["config"], "autotune_seconds": tune_s,
             "candidates": len(tune["table"])}
 

@@ -365,6 +365,7 @@ struct PairTile {
   int64_t a_off;   // global index of the A slice
   int64_t b_off;   // global index of the B slice
   int na, nb, count;
+  int flags;       // DescTiles only: bit 0 input in buf[1], bit 1 last level of its segment
 };
 
 // Where tile t of a merge pass lies: the first element of its pair of runs
@@ -379,6 +380,8 @@ struct PairSpan {
 // are order keys in and out (the kernel's DT_OUT maps them back).
 struct UniformRuns {
   static constexpr bool kMaps = false;
+  static constexpr bool kDesc = false;
+  static constexpr bool kAnyStart = false;   // pairs start at multiples of 2 run
   int64_t n, run, tpp;
   int dt_in = DT_U32, dt_out = DT_U32;   // unused
   __device__ __forceinline__ PairSpan span(int64_t t) const {
@@ -402,6 +405,8 @@ struct UniformRuns {
 constexpr int MAX_TABLE_PAIRS = 32;
 struct TableRuns {
   static constexpr bool kMaps = true;
+  static constexpr bool kDesc = false;
+  static constexpr bool kAnyStart = true;    // runs start anywhere
   int dt_in, dt_out;
   int npairs;
   int64_t first_tile[MAX_TABLE_PAIRS + 1];
@@ -424,6 +429,26 @@ struct TableRuns {
   }
 };
 
+// Merge tiles listed one by one in device memory (the merge levels of a
+// segmented batch): desc[t] is tile t's complete geometry, written by the
+// level's partition kernel, and *count the number of tiles.  Each tile
+// reads buf1 if flags bit 0 is set, else buf0, and writes the other buffer
+// (segments alternate buffers by the parity of their number of levels, so
+// that each one's last level lands in the output); tiles of a segment's
+// last level (flags bit 1) map their keys back to dt.
+template <typename K>
+struct DescTiles {
+  static constexpr bool kMaps = false;
+  static constexpr bool kDesc = true;
+  static constexpr bool kAnyStart = true;    // segments start anywhere
+  const PairTile *desc;
+  const unsigned long long *count;
+  K *buf0, *buf1;
+  uint32_t *vbuf0, *vbuf1;
+  int dt;
+  int dt_in = DT_U32, dt_out = DT_U32;   // unused: kMaps is false
+};
+
 // Geometry of tile t from its start splitter s0 and the next tile's s1
 // (s1 is ignored when the tile ends its pair).
 template <class GEOM>
@@ -443,6 +468,7 @@ __device__ __forceinline__ PairTile pair_tile_from(int64_t t, const GEOM &geom, 
   g.na = (int)(a1 - a0);
   g.count = (int)(out1 - g.out0);
   g.nb = g.count - g.na;
+  g.flags = 0;
   return g;
 }
 
@@ -607,14 +633,17 @@ template <int NT, int VT, int DT_OUT, bool PAIRS, typename K = uint32_t, bool SE
           class GEOM = UniformRuns>
 __global__ void __launch_bounds__(NT, PAIRS ? 3 : 4) merge_tma_kernel(
     const K *__restrict__ src, const uint32_t *__restrict__ vsrc, K *__restrict__ dst,
-    uint32_t *__restrict__ vdst, int64_t n, const GEOM geom, int64_t num_tiles,
+    uint32_t *__restrict__ vdst, int64_t n, const GEOM geom, int64_t num_tiles_arg,
     const int64_t *__restrict__ split, int *status, K *samp, int reverse) {
   pdl_wait();      // the previous kernel of the stream has finished writing
+  int64_t num_tiles = num_tiles_arg;
+  if constexpr (GEOM::kDesc) num_tiles = (int64_t)*geom.count;
   constexpr int TILE = NT * VT;
   constexpr int WOUT = 32 * VT;                       // outputs per warp
-  // staging stride per warp: a table of runs can start a warp's outputs
-  // anywhere, so its staging is shifted to the output's 16-byte phase
-  constexpr int WSTRIDE = WOUT + (GEOM::kMaps ? 16 / (int)sizeof(K) : 0);
+  // staging stride per warp: runs of any start (kAnyStart) can start a
+  // warp's outputs anywhere, so their staging is shifted to the output's
+  // 16-byte phase
+  constexpr int WSTRIDE = WOUT + (GEOM::kAnyStart ? 16 / (int)sizeof(K) : 0);
   constexpr int EPV = 16 / sizeof(K);                 // keys per 16 bytes
   // A window + gap, B window + gap, rounding slack
   constexpr int IN_LEN = (TILE + 2 * SENT + 16) & ~3;
@@ -639,21 +668,41 @@ __global__ void __launch_bounds__(NT, PAIRS ? 3 : 4) merge_tma_kernel(
   const int64_t n_al = n & ~int64_t(EPV - 1);
   const int64_t G = gridDim.x;
   int64_t t = blockIdx.x;
+  // the arrays a tile reads and writes (per tile for DescTiles)
+  auto ksrc_of = [&](const PairTile &g) -> const K * {
+    if constexpr (GEOM::kDesc) return (g.flags & 1) ? geom.buf1 : geom.buf0;
+    else return src;
+  };
+  auto vsrc_of = [&](const PairTile &g) -> const uint32_t * {
+    if constexpr (GEOM::kDesc) return (g.flags & 1) ? geom.vbuf1 : geom.vbuf0;
+    else return vsrc;
+  };
+  auto kdst_of = [&](const PairTile &g) -> K * {
+    if constexpr (GEOM::kDesc) return (g.flags & 1) ? geom.buf0 : geom.buf1;
+    else return dst;
+  };
+  auto vdst_of = [&](const PairTile &g) -> uint32_t * {
+    if constexpr (GEOM::kDesc) return (g.flags & 1) ? geom.vbuf0 : geom.vbuf1;
+    else return vdst;
+  };
   // loop index i -> tile: ascending, or descending when `reverse` (passes
   // alternate direction so that each pass starts where the previous one
   // ended, on data still in L2)
   auto tile_of = [&](int64_t i) { return reverse ? num_tiles - 1 - i : i; };
   int64_t pf0 = 0, pf1 = 0;   // thread 0: splitters of loop index t + G
+  [[maybe_unused]] PairTile pfd{};   // thread 0, DescTiles: the descriptor of loop index t + G
   [[maybe_unused]] int64_t own0 = 0, own1 = 0;   // SELF: the first tile's splitters (warp 0)
   // Self-partitioned: warp 0 finds the start splitter of tile u (lanes 0-15)
   // and of the next tile, u's end (lanes 16-31).
   [[maybe_unused]] auto self_split = [&](int64_t i, int64_t &s0, int64_t &s1) {
-    const int64_t v = tile_of(i) + (lane >> 4);
-    const unsigned gmask = 0xFFFFu << (lane & 16);
-    int64_t c = 0;
-    if (v < num_tiles) c = tile_corank_group<16>(src, geom, TILE, v, lane & 15, gmask);
-    s1 = __shfl_sync(0xffffffffu, c, 16);
-    s0 = c;
+    if constexpr (!GEOM::kDesc) {   // (descriptor lists carry their splitters)
+      const int64_t v = tile_of(i) + (lane >> 4);
+      const unsigned gmask = 0xFFFFu << (lane & 16);
+      int64_t c = 0;
+      if (v < num_tiles) c = tile_corank_group<16>(src, geom, TILE, v, lane & 15, gmask);
+      s1 = __shfl_sync(0xffffffffu, c, 16);
+      s0 = c;
+    }
   };
   if constexpr (SELF) {
     if (warp == 0 && t < num_tiles) self_split(t, own0, own1);
@@ -664,13 +713,18 @@ __global__ void __launch_bounds__(NT, PAIRS ? 3 : 4) merge_tma_kernel(
     fence_mbar_init();
     if (t < num_tiles) {
       const int64_t u = tile_of(t);
-      if constexpr (SELF)
+      if constexpr (GEOM::kDesc)
+        desc[0] = geom.desc[u];
+      else if constexpr (SELF)
         desc[0] = pair_tile_from(u, geom, TILE, own0, own1);
       else
         desc[0] = pair_tile_from(u, geom, TILE, split[u], u + 1 < num_tiles ? split[u + 1] : 0);
-      issue_tile(src, PAIRS ? vsrc : nullptr, n_al, desc[0], in_buf[0], vin_buf[0], &bar[0]);
+      issue_tile(ksrc_of(desc[0]), PAIRS ? vsrc_of(desc[0]) : nullptr, n_al, desc[0], in_buf[0],
+                 vin_buf[0], &bar[0]);
     }
-    if constexpr (!SELF) {
+    if constexpr (GEOM::kDesc) {
+      if (t + G < num_tiles) pfd = geom.desc[tile_of(t + G)];
+    } else if constexpr (!SELF) {
       if (t + G < num_tiles) {
         const int64_t u = tile_of(t + G);
         pf0 = split[u];
@@ -699,10 +753,13 @@ __global__ void __launch_bounds__(NT, PAIRS ? 3 : 4) merge_tma_kernel(
     }
     // every thread is past the previous tile: its buffer and descriptor are free
     if (tid == 0 && tn < num_tiles) {
-      desc[b ^ 1] = pair_tile_from(tile_of(tn), geom, TILE, pf0, pf1);
-      issue_tile(src, PAIRS ? vsrc : nullptr, n_al, desc[b ^ 1], in_buf[b ^ 1], vin_buf[b ^ 1],
-                 &bar[b ^ 1]);
-      if constexpr (!SELF) {   // (a self-partitioned pass has at most two tiles per CTA)
+      if constexpr (GEOM::kDesc) desc[b ^ 1] = pfd;
+      else desc[b ^ 1] = pair_tile_from(tile_of(tn), geom, TILE, pf0, pf1);
+      issue_tile(ksrc_of(desc[b ^ 1]), PAIRS ? vsrc_of(desc[b ^ 1]) : nullptr, n_al, desc[b ^ 1],
+                 in_buf[b ^ 1], vin_buf[b ^ 1], &bar[b ^ 1]);
+      if constexpr (GEOM::kDesc) {
+        if (tn + G < num_tiles) pfd = geom.desc[tile_of(tn + G)];
+      } else if constexpr (!SELF) {   // (a self-partitioned pass has at most two tiles per CTA)
         const int64_t tp = tn + G;
         if (tp < num_tiles) {
           const int64_t u = tile_of(tp);
@@ -712,6 +769,10 @@ __global__ void __launch_bounds__(NT, PAIRS ? 3 : 4) merge_tma_kernel(
       }
     }
     const PairTile g = desc[b];
+    const K *tsrc = ksrc_of(g);
+    const uint32_t *tvsrc = vsrc_of(g);
+    K *tdst = kdst_of(g);
+    uint32_t *tvdst = vdst_of(g);
     const SmemSlices l = smem_slices<K>(g);
     K *s = in_buf[b];
     uint32_t *sv = vin_buf[b];
@@ -734,14 +795,14 @@ __global__ void __launch_bounds__(NT, PAIRS ? 3 : 4) merge_tma_kernel(
       if (lane < EPV - 1) {
         const int64_t i = (g.a_off > n_al ? g.a_off : n_al) + lane;
         if (i < g.a_off + g.na) {
-          s[a0 + (int)(i - g.a_off)] = to_key(__ldg(src + i), GEOM::kMaps ? geom.dt_in : DT_U32);
-          if (PAIRS) sv[a0 + (int)(i - g.a_off)] = __ldg(vsrc + i);
+          s[a0 + (int)(i - g.a_off)] = to_key(__ldg(tsrc + i), GEOM::kMaps ? geom.dt_in : DT_U32);
+          if (PAIRS) sv[a0 + (int)(i - g.a_off)] = __ldg(tvsrc + i);
         }
       } else if (lane < 2 * (EPV - 1)) {
         const int64_t i = (g.b_off > n_al ? g.b_off : n_al) + (lane - (EPV - 1));
         if (i < g.b_off + g.nb) {
-          s[b0 + (int)(i - g.b_off)] = to_key(__ldg(src + i), GEOM::kMaps ? geom.dt_in : DT_U32);
-          if (PAIRS) sv[b0 + (int)(i - g.b_off)] = __ldg(vsrc + i);
+          s[b0 + (int)(i - g.b_off)] = to_key(__ldg(tsrc + i), GEOM::kMaps ? geom.dt_in : DT_U32);
+          if (PAIRS) sv[b0 + (int)(i - g.b_off)] = __ldg(tvsrc + i);
         }
       }
     }
@@ -767,12 +828,14 @@ __global__ void __launch_bounds__(NT, PAIRS ? 3 : 4) merge_tma_kernel(
     const int wcount = g.count - w0 < WOUT ? g.count - w0 : WOUT;
     const int64_t gb = g.out0 + w0;                  // the warp's first output
     // sh: gb's offset past a 16-byte boundary, 0 for the uniform runs of a sort
-    const int sh = GEOM::kMaps ? (int)(gb & (EPV - 1)) : 0;
+    const int sh = GEOM::kAnyStart ? (int)(gb & (EPV - 1)) : 0;
     K *ws = wout + sh;
     uint32_t *wvs = wvout + sh;
     if (lane == 0) bulk_wait_read_all();   // the warp's previous stores have left its slices
     __syncwarp();
-    const int dt_out = GEOM::kMaps ? geom.dt_out : DT_OUT;   // a constant unless GEOM maps
+    int dt_out = DT_OUT;   // a constant unless GEOM maps at run time
+    if constexpr (GEOM::kMaps) dt_out = geom.dt_out;
+    if constexpr (GEOM::kDesc) dt_out = (g.flags & 2) ? geom.dt : (sizeof(K) == 8 ? DT_U64 : DT_U32);
     if (g.count == TILE) {
 #pragma unroll
       for (int k = 0; k < VT; ++k) {
@@ -804,17 +867,17 @@ __global__ void __launch_bounds__(NT, PAIRS ? 3 : 4) merge_tma_kernel(
       const int body = (wcount - head) & ~(EPV - 1);
       const int tail = wcount - head - body;
       if (lane == 0 && body) {
-        bulk_store(dst + gb + head, ws + head, (uint32_t)body * (uint32_t)sizeof(K));
-        if (PAIRS) bulk_store(vdst + gb + head, wvs + head, (uint32_t)body * 4u);
+        bulk_store(tdst + gb + head, ws + head, (uint32_t)body * (uint32_t)sizeof(K));
+        if (PAIRS) bulk_store(tvdst + gb + head, wvs + head, (uint32_t)body * 4u);
         bulk_commit();
       }
       if (lane < head) {
-        dst[gb + lane] = ws[lane];
-        if (PAIRS) vdst[gb + lane] = wvs[lane];
+        tdst[gb + lane] = ws[lane];
+        if (PAIRS) tvdst[gb + lane] = wvs[lane];
       }
       if (lane < tail) {
-        dst[gb + head + body + lane] = ws[head + body + lane];
-        if (PAIRS) vdst[gb + head + body + lane] = wvs[head + body + lane];
+        tdst[gb + head + body + lane] = ws[head + body + lane];
+        if (PAIRS) tvdst[gb + head + body + lane] = wvs[head + body + lane];
       }
     }
   }
@@ -1413,7 +1476,9 @@ static int64_t fill_run_table(const int64_t *off, int nr, int tile, int dt_in, i
   return tiles;
 }
 
-template <typename K, bool PAIRS>
+// Opts kernel fn (one per GEOM, K, PAIRS) in to its dynamic shared memory,
+// once per device.
+template <class GEOM, typename K, bool PAIRS>
 static void table_merge_attrs(const void *fn, size_t smem) {
   static std::atomic<uint64_t> done_mask{0};
   int dev = 0;
@@ -1441,7 +1506,7 @@ static void launch_table_pass(const K *src, const uint32_t *vsrc, K *dst, uint32
                           (size_t)(NT / 32) * 16 * (PAIRS ? 2 : 1);
   constexpr int DT0 = WIDE ? DT_U64 : DT_U32;   // unused: TableRuns maps at run time
   auto kernel = merge_tma_kernel<NT, VT, DT0, PAIRS, K, false, TableRuns>;
-  table_merge_attrs<K, PAIRS>((const void *)kernel, SMEM);
+  table_merge_attrs<TableRuns, K, PAIRS>((const void *)kernel, SMEM);
   const unsigned grid = (unsigned)tma_merge_grid(tiles, PAIRS ? 1 : (WIDE ? 2 : 0));
   {
     TraceScope tr(TK_PARTITION, st);
@@ -1506,6 +1571,126 @@ static int merge_runs_typed(const K *kin, const uint32_t *vin, K *kout, uint32_t
     vsrc = vdst;
   }
   return rc;
+}
+
+// ---- the merge levels of a segmented batch ------------------------------
+//
+// Level k merges, in every large segment with at least k merge levels, the
+// runs of tile * 2^(k-1) keys pairwise (the level-0 runs are the segment's
+// tile sorts).  Three launches per level: one thread per segment reserves
+// its merge tiles and lists them as (segment, tile in the segment); one
+// thread per listed tile computes the tile's geometry from its two
+// merge-path splitters and writes it as a descriptor; the persistent
+// bulk-copy merge kernel then runs over the descriptors (DescTiles).
+
+int seg_merge_tile(bool pairs) { return pairs ? TMA_PMERGE_TILE : TMA_MERGE_TILE; }
+size_t seg_tile_desc_bytes() { return sizeof(PairTile); }
+
+__device__ __forceinline__ int ceil_log2_i64(int64_t x) {
+  int p = 0;
+  while ((int64_t(1) << p) < x) ++p;
+  return p;
+}
+
+__global__ void seg_describe_kernel(const int64_t *__restrict__ off, int64_t nseg,
+                                    int64_t min_len, int tile, int k, int mt,
+                                    const int *status, unsigned long long *count,
+                                    int64_t *__restrict__ tile_seg) {
+  pdl_wait();      // the previous kernel of the stream has finished writing
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nseg || *status != NSORT_OK) return;
+  const int64_t L = off[s + 1] - off[s];
+  if (L <= min_len || ceil_log2_i64((L + tile - 1) / tile) < k) return;
+  const int64_t run = (int64_t)tile << (k - 1);
+  const int64_t tpp = (2 * run + mt - 1) / mt;
+  const int64_t full = L / (2 * run);
+  const int64_t tiles = full * tpp + (L - full * 2 * run + mt - 1) / mt;
+  const int64_t base = (int64_t)atomicAdd(count, (unsigned long long)tiles);
+  for (int64_t j = 0; j < tiles; ++j) tile_seg[base + j] = (s << 32) | j;
+}
+
+template <typename K>
+__global__ void seg_partition_kernel(const int64_t *__restrict__ off, int tile, int k, int mt,
+                                     const unsigned long long *count,
+                                     const int64_t *__restrict__ tile_seg,
+                                     const K *buf0, const K *buf1, PairTile *__restrict__ desc) {
+  pdl_wait();      // the previous kernel of the stream has finished writing
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)*count) return;
+  const int64_t e = tile_seg[t];
+  const int64_t sid = e >> 32, j = e & 0xFFFFFFFFll;
+  const int64_t o = off[sid];
+  const int64_t L = off[sid + 1] - o;
+  const int P = ceil_log2_i64((L + tile - 1) / tile);
+  const int64_t run = (int64_t)tile << (k - 1);
+  const int64_t tpp = (2 * run + mt - 1) / mt;
+  const int64_t pair = j / tpp, jj = j - pair * tpp;
+  const int64_t pair0 = pair * 2 * run;
+  const int64_t la = L - pair0 < run ? L - pair0 : run;
+  const int64_t rest = L - pair0 - run;
+  const int64_t lb = rest <= 0 ? 0 : (rest < run ? rest : run);
+  const int64_t d0 = jj * mt;
+  const int64_t d1 = d0 + mt < la + lb ? d0 + mt : la + lb;
+  const int in1 = (P - (k - 1)) & 1;   // level k-1 of this segment is in buf1
+  const K *A = (in1 ? buf1 : buf0) + o + pair0;
+  const K *B = A + la;
+  int64_t a0 = merge_path_global(A, la, B, lb, d0);
+  int64_t a1 = d1 == la + lb ? la : merge_path_global(A, la, B, lb, d1);
+  clamp_coranks(la, lb, d0, d1, a0, a1);
+  PairTile g;
+  g.out0 = o + pair0 + d0;
+  g.a_off = o + pair0 + a0;
+  g.b_off = o + pair0 + la + (d0 - a0);
+  g.na = (int)(a1 - a0);
+  g.count = (int)(d1 - d0);
+  g.nb = g.count - g.na;
+  g.flags = in1 | (k == P ? 2 : 0);
+  desc[t] = g;
+}
+
+template <bool PAIRS>
+static void launch_seg_level_merge(const SegLevelArgs &a, cudaStream_t st) {
+  using K = uint32_t;
+  constexpr int NT = PAIRS ? TMA_PMERGE_NT : TMA_MERGE_NT;
+  constexpr int VT = PAIRS ? TMA_PMERGE_VT : TMA_MERGE_VT;
+  constexpr size_t SMEM = (PAIRS ? TMA_PMERGE_SMEM : TMA_MERGE_SMEM) +
+                          (size_t)(NT / 32) * 16 * (PAIRS ? 2 : 1);   // shifted staging
+  auto kernel = merge_tma_kernel<NT, VT, DT_U32, PAIRS, K, false, DescTiles<K>>;
+  table_merge_attrs<DescTiles<K>, K, PAIRS>((const void *)kernel, SMEM);
+  const unsigned grid = (unsigned)tma_merge_grid(a.max_tiles, PAIRS ? 1 : 0);
+  DescTiles<K> geom;
+  geom.desc = static_cast<const PairTile *>(a.desc);
+  geom.count = a.count;
+  geom.buf0 = a.kout;
+  geom.buf1 = a.ktmp;
+  geom.vbuf0 = a.vout;
+  geom.vbuf1 = a.vtmp;
+  geom.dt = a.dt;
+  TraceScope tr(TK_SEG_MERGE, st);
+  const int64_t *no_split = nullptr;
+  K *no_samples = nullptr;
+  launch_pdl(kernel, grid, NT, SMEM, st, (const K *)a.kout, (const uint32_t *)a.vout, a.ktmp,
+             a.vtmp, a.n, geom, (int64_t)0, no_split, a.status, no_samples, 0);
+}
+
+int launch_segmented_level(const SegLevelArgs &a, cudaStream_t st) {
+  const bool pairs = a.vout != nullptr;
+  const int mt = seg_merge_tile(pairs);
+  {
+    TraceScope tr(TK_SEG_BIN, st);
+    launch_pdl(seg_describe_kernel, (unsigned)((a.nseg + 255) / 256), 256, 0, st, a.off, a.nseg,
+               a.min_len, a.tile, a.k, mt, (const int *)a.status, a.count, a.tile_seg);
+  }
+  {
+    TraceScope tr(TK_PARTITION, st);
+    launch_pdl(seg_partition_kernel<uint32_t>, (unsigned)((a.max_tiles + 255) / 256), 256, 0, st,
+               a.off, a.tile, a.k, mt, (const unsigned long long *)a.count,
+               (const int64_t *)a.tile_seg, (const uint32_t *)a.kout, (const uint32_t *)a.ktmp,
+               static_cast<PairTile *>(a.desc));
+  }
+  if (pairs) launch_seg_level_merge<true>(a, st);
+  else launch_seg_level_merge<false>(a, st);
+  return launch_status("segmented merge level");
 }
 
 int merge_runs_impl(const void *kin, const uint32_t *vin, void *kout, uint32_t *vout,

@@ -41,6 +41,28 @@ int sort_pairs_impl(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, ui
 
 size_t segmented_temp_bytes(int kind, uint64_t n, uint64_t nseg);
 
+// One merge level of the large segments of a segmented batch, as bulk-copy
+// merge passes over per-tile descriptors (nsort_segmented).  Segments longer
+// than min_len were sorted in tiles of `tile` keys (level 0); level k
+// merges their runs of tile * 2^(k-1) keys.  Level k-1 of a segment with P
+// levels is in ktmp when P - (k-1) is odd, else in kout.
+struct SegLevelArgs {
+  const int64_t *off;          // nseg + 1 segment offsets (device)
+  int64_t nseg, n;
+  int64_t min_len;
+  int tile, k, dt;
+  uint32_t *kout, *ktmp;
+  uint32_t *vout, *vtmp;       // both null for keys only
+  int *status;                 // device status word (NSORT_OK: offsets are valid)
+  unsigned long long *count;   // device counter of this level's tiles, zero before the call
+  int64_t *tile_seg;           // device scratch, max_tiles entries
+  void *desc;                  // device scratch, max_tiles descriptors
+  int64_t max_tiles;
+};
+int seg_merge_tile(bool pairs);
+size_t seg_tile_desc_bytes();
+int launch_segmented_level(const SegLevelArgs &a, cudaStream_t st);
+
 // Merge of sorted runs of any lengths (nsort_merge_shards).
 size_t merge_runs_temp_bytes(bool pairs, uint64_t n, uint64_t nruns, int dtype);
 int merge_runs_impl(const void *kin, const uint32_t *vin, void *kout, uint32_t *vout,

@@ -1,4 +1,4 @@
-// nsort_segmented: many independent arrays sorted in one persistent launch.
+// nsort_segmented: many independent arrays sorted in one batch.
 //
 // Segments are binned by length on the device:
 //   tiny   L <= W_t          one thread sorts the segment in registers with
@@ -10,20 +10,17 @@
 //   large  L >  16 NT        tile sorts of the segment's TILE-key tiles
 //                            (level 0; keys take 32 per thread, TILE = 32 NT,
 //                            pairs 16, TILE = 16 NT), then one merge level per
-//                            doubling of the run length, each split into
-//                            merge tiles of 16 NT outputs with their own
-//                            merge-path splitters.
-// A persistent kernel takes work items from a queue (one atomic counter):
-// [level-0 tiles of all large segments][medium][small batches][tiny
-// batches][level-1 merge tiles][level-2]...  Each large segment counts its
-// finished items and splitter phases.  The CTA that finishes the last item
-// of a level computes the merge-path splitters of all the next level's
-// merge tiles of that segment (a warp per splitter) and counts one more; a
-// merge tile of level k waits until every level k-1 item and the level-k
-// splitter phase of its segment are done (bounded waiting), then reads its
-// two splitters.  Items are taken in queue order and only wait on items
-// earlier in the queue, or on the splitter phase run by the CTA that
-// finished the last of them, so the waits always end.
+//                            doubling of the run length.
+// A persistent kernel takes the level-0 tiles and the medium, small and tiny
+// segments from a queue (one atomic counter):
+// [level-0 tiles of all large segments][medium][small batches][tiny batches].
+// The merge levels then run as the plain sort's bulk-copy merge passes over
+// lists of merge tiles (launch_segmented_level): level k merges, in every
+// segment with at least k levels, its runs of TILE * 2^(k-1) keys pairwise.
+// Every step is stream-ordered, with no host synchronisation, so a batch can
+// be captured into a CUDA graph: the host launches as many levels as the
+// longest possible segment could need, and levels past the batch's longest
+// segment find no tiles.
 //
 // The tunables (block size NT, tiny network width W_t, small-bin IPT, CTAs
 // per SM) come from nsort_segmented_set_config, fed by the autotuner.
@@ -53,8 +50,8 @@ struct Ctrl {
   unsigned long long n_tiny, n_small, n_medium;
   unsigned long long bucket_tiles[MAXLV + 1];   // tiles of large segments needing b levels
   unsigned long long bucket_base[MAXLV + 2];    // exclusive prefix of bucket_tiles
-  unsigned long long q_medium, q_small, q_tiny, q_merge, q_total;
-  unsigned long long q_level[MAXLV + 2];        // first queue item of merge level k >= 1
+  unsigned long long q_medium, q_small, q_tiny, q_total;
+  unsigned long long lvl_count[MAXLV + 2];      // merge tiles of level k (launch_segmented_level)
 };
 
 struct Params {
@@ -72,13 +69,10 @@ struct Params {
   int *small_list;
   int *medium_list;
   int64_t *slot_base;    // large segment -> first slot of its tiles
-  int64_t *split;        // slot -> merge-path splitter of that merge tile (current level)
-  unsigned long long *done;   // large segment -> finished items and splitter phases
   int *owner;            // slot -> large segment
   int dt;
   int tile;              // keys per level-0 tile: NT * 32 (keys) or NT * 16 (pairs)
-  int mt;                // outputs per merge tile: NT * 16
-  int r;                 // merge tiles per level-0 tile: tile / mt
+  int mt;                // longest medium segment: NT * 16
   int nt;
   int tiny_w;            // 8 or 16
   int small_ipt;         // 8 or 16
@@ -136,14 +130,7 @@ __global__ void seg_plan_kernel(Params p) {
   c->q_small = c->q_medium + c->n_medium;
   const unsigned long long warps = p.nt / 32;
   c->q_tiny = c->q_small + (c->n_small + warps - 1) / warps;
-  c->q_merge = c->q_tiny + (c->n_tiny + p.nt - 1) / p.nt;
-  unsigned long long q = c->q_merge;
-  for (int k = 1; k <= maxlv; ++k) {
-    c->q_level[k] = q;
-    q += (base - c->bucket_base[k]) * (unsigned long long)p.r;   // r merge tiles per tile
-  }
-  c->q_level[maxlv + 1] = q;
-  c->q_total = q;
+  c->q_total = c->q_tiny + (c->n_tiny + p.nt - 1) / p.nt;
   c->max_level = maxlv;
 }
 
@@ -158,10 +145,7 @@ __global__ void seg_owner_kernel(Params p) {
   const int64_t T = (L + p.tile - 1) / p.tile;
   const int64_t g = (int64_t)p.ctrl->bucket_base[ceil_log2(T)] + p.slot_base[w];
   __syncwarp();
-  if (lane == 0) {
-    p.slot_base[w] = g;
-    p.done[w] = 0;
-  }
+  if (lane == 0) p.slot_base[w] = g;
   for (int64_t i = lane; i < T; i += 32) p.owner[g + i] = (int)w;
 }
 
@@ -361,215 +345,28 @@ __device__ void thread_sort_segment(const Params &p, int64_t sid) {
   }
 }
 
-// Stages slices [a_off, a_off+na) and [b_off, ...) of src into s with loads
-// that see other CTAs' earlier stores (the merge levels of large segments).
-template <int NT, int VT>
-__device__ __forceinline__ void stage_slices_cg(uint32_t *s, const uint32_t *src, int64_t a_off,
-                                                int64_t b_off, int na, int count) {
-  const int tid = threadIdx.x;
-  const uint32_t *pa = src + a_off + tid;
-  const uint32_t *pb = src + b_off + (tid - na);
-  uint32_t t[VT];
-#pragma unroll
-  for (int j = 0; j < VT; ++j) {
-    const int i = tid + NT * j;
-    uint32_t v = 0;
-    if (i < na) v = __ldcg(pa + NT * j);
-    else if (i < count) v = __ldcg(pb + NT * j);
-    t[j] = v;
-  }
-  const int sbase = pidx<uint32_t>(tid);
-#pragma unroll
-  for (int j = 0; j < VT; ++j) s[sbase + j * (NT + NT / 32)] = t[j];
-}
-
-// Buffer that level `level` of a large segment with P merge levels writes
-// (level 0: the tile sorts): the levels alternate so that level P ends in
-// the output.
-__device__ __forceinline__ bool level_in_tmp(int P, int level) { return ((P - level) & 1) != 0; }
-
-// Item counts of a large segment of L keys: T level-0 tiles, Tm non-empty
-// merge tiles per merge level (the queue holds r * T merge items per level;
-// those past the segment's end do nothing and are not counted), P levels.
-struct SegShape {
-  int64_t off, L, T, Tm;
-  int P;
-};
-__device__ __forceinline__ SegShape seg_shape(const Params &p, int64_t sid) {
-  SegShape g;
-  g.off = p.off[sid];
-  g.L = p.off[sid + 1] - g.off;
-  g.T = (g.L + p.tile - 1) / p.tile;
-  g.Tm = (g.L + p.mt - 1) / p.mt;
-  g.P = ceil_log2(g.T);
-  return g;
-}
-// Counter value once every item of levels 0..k-1 and the splitter phases
-// 1..k-1 are done.
-__device__ __forceinline__ unsigned long long level_done(const SegShape &g, int k) {
-  return (unsigned long long)(g.T + (int64_t)(k - 1) * g.Tm + (k - 1));
-}
-
-// Marks one item of large segment sid, of level `level` (0: a tile sort),
-// finished: the CTA's stores are ordered before one thread's fence and
-// counter update.  If that finished the level (the counter reached
-// level_done(level + 1)), this CTA computes the merge-path splitters of every
-// merge tile of level + 1, one warp per splitter, and counts the phase.
-// Items of the segment's last level are not counted: nothing waits on them.
-template <int NT>
-__device__ void finish_item(const Params &p, int *plan_sh, int64_t sid, int level) {
-  const SegShape g = seg_shape(p, sid);
-  if (level == g.P) return;
-  // the barrier orders every thread's stores before thread 0's fence and
-  // counter update (the release pattern of a grid-wide barrier)
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned long long old = atomicAdd(&p.done[sid], 1ull);
-    const int k = level + 1;
-    *plan_sh = (k <= g.P && old + 1 == level_done(g, k)) ? k : 0;
-  }
-  __syncthreads();
-  const int k = *plan_sh;
-  if (k == 0) return;
-  const int lane = threadIdx.x & 31;
-  const int64_t run = (int64_t)p.tile << (k - 1);
-  const uint32_t *ksrc = (level_in_tmp(g.P, k - 1) ? p.ktmp : p.kout) + g.off;
-  const int64_t s0 = p.slot_base[sid] * p.r;
-  for (int64_t m = threadIdx.x >> 5; m < g.Tm; m += NT / 32) {
-    const int64_t out0 = m * p.mt;
-    const int64_t pair0 = out0 & ~(2 * run - 1);
-    const int64_t la = g.L - pair0 < run ? g.L - pair0 : run;
-    const int64_t rest = g.L - pair0 - run;
-    const int64_t lb = rest <= 0 ? 0 : (rest < run ? rest : run);
-    const int64_t r = out0 == pair0 ? 0
-                                    : merge_path_global_warp<true>(ksrc + pair0, la,
-                                                                   ksrc + pair0 + la, lb,
-                                                                   out0 - pair0, lane);
-    if (lane == 0) p.split[s0 + m] = r;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(&p.done[sid], 1ull);
-  }
-}
-
-// Merge tile m (16 NT outputs) of level `level` of large segment sid.
-template <int NT, bool PAIRS>
-__device__ void merge_tile(const Params &p, void *smem, int *plan_sh, int64_t sid, int level,
-                           int64_t m) {
-  constexpr int VT = 16;
-  constexpr int MT = NT * VT;
-  const int tid = threadIdx.x;
-  const SegShape g = seg_shape(p, sid);
-  if (m >= g.Tm) return;   // past the segment's end: nothing to merge, not counted
-  const int64_t off = g.off;
-  const int64_t L = g.L;
-  const int P = g.P;
-  if (tid == 0)   // levels 0..level-1 and this level's splitter phase done
-    wait_at_least(&p.done[sid], level_done(g, level) + 1, &p.ctrl->status, 2000000000ull);
-  __syncthreads();
-  const bool src_tmp = level_in_tmp(P, level - 1);
-  const bool dst_tmp = level_in_tmp(P, level);
-  const uint32_t *ksrc = (src_tmp ? p.ktmp : p.kout) + off;
-  uint32_t *kdst = (dst_tmp ? p.ktmp : p.kout) + off;
-  const int64_t run = (int64_t)p.tile << (level - 1);
-  const int64_t out0 = m * MT;
-  const int64_t out1 = out0 + MT < L ? out0 + MT : L;
-  const int64_t pair0 = out0 & ~(2 * run - 1);
-  const int64_t la = L - pair0 < run ? L - pair0 : run;
-  const int64_t rest = L - pair0 - run;
-  const int64_t lb = rest <= 0 ? 0 : (rest < run ? rest : run);
-  const int64_t pair_end = pair0 + la + lb;
-  const int64_t s0 = p.slot_base[sid] * p.r;
-  int64_t a_beg = __ldcg(p.split + s0 + m);
-  int64_t a_end = out1 == pair_end ? la : __ldcg(p.split + s0 + m + 1);
-  {
-    // keep both slices inside their runs and summing to the tile, whatever the
-    // splitters say (they are exact for sorted runs)
-    const int64_t d0 = out0 - pair0, d1 = out1 - pair0;
-    const int64_t lo0 = d0 - lb > 0 ? d0 - lb : 0, hi0 = d0 < la ? d0 : la;
-    a_beg = a_beg < lo0 ? lo0 : (a_beg > hi0 ? hi0 : a_beg);
-    const int64_t lo1 = d1 - lb > a_beg ? d1 - lb : a_beg;
-    const int64_t hi1 = a_beg + (d1 - d0) < la ? a_beg + (d1 - d0) : la;
-    a_end = a_end < lo1 ? lo1 : (a_end > hi1 ? hi1 : a_end);
-  }
-  const int na = (int)(a_end - a_beg);
-  const int count = (int)(out1 - out0);
-  const int nb = count - na;
-  const int64_t a_off = pair0 + a_beg;
-  const int64_t b_off = pair0 + la + (out0 - pair0 - a_beg);
-  uint32_t *sk = static_cast<uint32_t *>(smem);
-  uint32_t *sv = sk + merge_smem_len<uint32_t>(MT, VT);
-  stage_slices_cg<NT, VT>(sk, ksrc, a_off, b_off, na, count);
-  if (PAIRS) {
-    const uint32_t *vsrc = (src_tmp ? p.vtmp : p.vout) + off;
-    stage_slices_cg<NT, VT>(sv, vsrc, a_off, b_off, na, count);
-  }
-  __syncthreads();
-  const int diag = tid * VT < count ? tid * VT : count;
-  const int ai = merge_path_smem(sk, 0, na, na, nb, diag);
-  uint32_t o[VT];
-  int from[VT];
-  serial_merge<VT, PAIRS>(sk, ai, na, na + diag - ai, count, o, from);
-  const int dto = level == P ? p.dt : (int)DT_U32;
-  const int e0 = tid * VT;
-  uint32_t ov[VT];
-  if (PAIRS) {
-#pragma unroll
-    for (int k = 0; k < VT; ++k) ov[k] = sv[pidx<uint32_t>(from[k])];
-  }
-  // thread t holds outputs [VT t, VT t + VT): staged in shared memory so
-  // that the global stores are coalesced
-  __syncthreads();   // every thread is done reading the staged slices
-#pragma unroll
-  for (int k = 0; k < VT; ++k) {
-    if (e0 + k < count) {
-      sk[pidx<uint32_t>(e0 + k)] = from_key(o[k], dto);
-      if (PAIRS) sv[pidx<uint32_t>(e0 + k)] = ov[k];
-    }
-  }
-  __syncthreads();
-  uint32_t *vdst = PAIRS ? (dst_tmp ? p.vtmp : p.vout) + off : nullptr;
-#pragma unroll
-  for (int j = 0; j < VT; ++j) {
-    const int e = tid + NT * j;
-    if (e < count) {
-      kdst[out0 + e] = sk[pidx<uint32_t>(e)];
-      if (PAIRS) vdst[out0 + e] = sv[pidx<uint32_t>(e)];
-    }
-  }
-  finish_item<NT>(p, plan_sh, sid, level);
-}
-
 template <int NT, bool PAIRS>
 __global__ void __launch_bounds__(NT, PAIRS ? 1 : 2) seg_sort_kernel(Params p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ unsigned long long item_sh;
-  __shared__ int plan_sh;
   // The queue's bin boundaries live in shared memory and are read per item:
   // held in registers for the whole loop they would cost the tile sorts
   // (at 2 CTAs of 512 threads, 64 registers a thread) registers they need.
-  __shared__ unsigned long long q_sh[5];   // medium, small, tiny, merge, total
-  __shared__ int max_level_sh;
+  __shared__ unsigned long long q_sh[4];   // medium, small, tiny, total
   const int tid = threadIdx.x;
   Ctrl *c = p.ctrl;
   if (tid == 0) {
     q_sh[0] = c->q_medium;
     q_sh[1] = c->q_small;
     q_sh[2] = c->q_tiny;
-    q_sh[3] = c->q_merge;
-    q_sh[4] = c->q_total;
-    max_level_sh = c->max_level;
+    q_sh[3] = c->q_total;
   }
   for (;;) {
     if (tid == 0) item_sh = atomicAdd(&c->next_item, 1ull);
     __syncthreads();
     const unsigned long long item = item_sh;
     const unsigned long long q_medium = q_sh[0], q_small = q_sh[1], q_tiny = q_sh[2],
-                             q_merge = q_sh[3], q_total = q_sh[4];
-    const int max_level = max_level_sh;
+                             q_total = q_sh[3];
     __syncthreads();
     if (item >= q_total) break;
     if (item < q_medium) {
@@ -586,7 +383,6 @@ __global__ void __launch_bounds__(NT, PAIRS ? 1 : 2) seg_sort_kernel(Params p) {
       uint32_t *vd = (P & 1) ? p.vtmp : p.vout;
       if (PAIRS) block_sort_range<NT, PAIRS>(p, smem_raw, off + b0, count, NT * 16, kd, vd, P == 0);
       else tile_sort32_range<NT>(p, smem_raw, off + b0, count, kd, P == 0);
-      finish_item<NT>(p, &plan_sh, sid, 0);
     } else if (item < q_small) {
       const int sid = p.medium_list[item - q_medium];
       const int64_t off = p.off[sid];
@@ -601,21 +397,13 @@ __global__ void __launch_bounds__(NT, PAIRS ? 1 : 2) seg_sort_kernel(Params p) {
         if (p.small_ipt == 8) warp_sort_segment<8, PAIRS>(p, sid);
         else warp_sort_segment<16, PAIRS>(p, sid);
       }
-    } else if (item < q_merge) {
+    } else {
       const unsigned long long idx = (item - q_tiny) * NT + tid;
       if (idx < c->n_tiny) {
         const int sid = p.tiny_list[idx];
         if (p.tiny_w == 8) thread_sort_segment<8, PAIRS>(p, sid);
         else thread_sort_segment<16, PAIRS>(p, sid);
       }
-    } else {
-      int k = 1;
-      while (k < max_level && item >= c->q_level[k + 1]) ++k;
-      const unsigned long long j = item - c->q_level[k];
-      const unsigned long long slot = c->bucket_base[k] + j / (unsigned)p.r;
-      const int sid = p.owner[slot];
-      const int64_t m = ((int64_t)slot - p.slot_base[sid]) * p.r + (int64_t)(j % (unsigned)p.r);
-      merge_tile<NT, PAIRS>(p, smem_raw, &plan_sh, sid, k, m);
     }
   }
 }
@@ -623,7 +411,8 @@ __global__ void __launch_bounds__(NT, PAIRS ? 1 : 2) seg_sort_kernel(Params p) {
 // ---- host side -------------------------------------------------------------
 
 struct Layout {
-  size_t ctrl, keys, vals, tiny, small, medium, slot, done, owner, split, total;
+  size_t ctrl, keys, vals, tiny, small, medium, slot, owner, tile_seg, desc, total;
+  int64_t max_tiles;   // merge tiles one level can have
 };
 
 Layout layout(uint64_t n, uint64_t nseg, bool pairs) {
@@ -641,9 +430,12 @@ Layout layout(uint64_t n, uint64_t nseg, bool pairs) {
   l.small = take(nseg * 4);
   l.medium = take(nseg * 4);
   l.slot = take(nseg * 8);
-  l.done = take(nseg * 8);
   l.owner = take((2 * (n / MIN_TILE) + 2) * 4);
-  l.split = take((2 * (n / MIN_TILE) + 2) * 2 * 8);   // up to two merge tiles per slot
+  // a segment of L keys has at most L / merge tile + (pairs of runs) + 1
+  // merge tiles in a level, and at most L / MIN_TILE / 2 + 1 pairs of runs
+  l.max_tiles = (int64_t)(n / (uint64_t)seg_merge_tile(pairs) + n / MIN_TILE + 2 * nseg + 16);
+  l.tile_seg = take((size_t)l.max_tiles * 8);
+  l.desc = take((size_t)l.max_tiles * seg_tile_desc_bytes());
   l.total = o;
   return l;
 }
@@ -656,9 +448,7 @@ size_t smem_bytes() {
   using K = typename std::conditional<PAIRS, uint64_t, uint32_t>::type;
   const size_t tile_b = sizeof(K) * merge_smem_len<K>(NT * 16, 16);
   const size_t tile32_b = PAIRS ? 0 : sizeof(uint32_t) * block_smem_len<uint32_t>(NT, 32);
-  const size_t merge_b = sizeof(uint32_t) * 2 * merge_smem_len<uint32_t>(NT * 16, 16);
-  size_t m = tile_b > merge_b ? tile_b : merge_b;
-  return m > tile32_b ? m : tile32_b;
+  return tile_b > tile32_b ? tile_b : tile32_b;
 }
 
 template <int NT, bool PAIRS>
@@ -749,14 +539,11 @@ extern "C" int nsort_segmented(const void *d_keys_in, void *d_keys_out, const ui
   p.small_list = reinterpret_cast<int *>(t + l.small);
   p.medium_list = reinterpret_cast<int *>(t + l.medium);
   p.slot_base = reinterpret_cast<int64_t *>(t + l.slot);
-  p.done = reinterpret_cast<unsigned long long *>(t + l.done);
   p.owner = reinterpret_cast<int *>(t + l.owner);
-  p.split = reinterpret_cast<int64_t *>(t + l.split);
   p.dt = dtype;
   p.nt = cfg.block_threads;
   p.mt = cfg.block_threads * 16;
   p.tile = pairs ? p.mt : cfg.block_threads * 32;
-  p.r = p.tile / p.mt;
   p.tiny_w = cfg.tiny_width;
   p.small_ipt = cfg.small_ipt;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -781,6 +568,33 @@ extern "C" int nsort_segmented(const void *d_keys_in, void *d_keys_out, const ui
   if (e != cudaSuccess) {
     set_last_error(std::string("nsort_segmented: ") + cudaGetErrorString(e));
     return NSORT_ECUDA;
+  }
+  // the merge levels: as many as a segment of all n keys would need (the
+  // host does not know the batch's longest segment; later levels find no
+  // tiles)
+  const int64_t tiles0 = ((int64_t)n + p.tile - 1) / p.tile;
+  int levels = 0;
+  while ((int64_t(1) << levels) < tiles0) ++levels;
+  SegLevelArgs a;
+  a.off = d_offsets;
+  a.nseg = (int64_t)nseg;
+  a.n = (int64_t)n;
+  a.min_len = p.mt;
+  a.tile = p.tile;
+  a.dt = dtype;
+  a.kout = p.kout;
+  a.ktmp = p.ktmp;
+  a.vout = pairs ? p.vout : nullptr;
+  a.vtmp = pairs ? p.vtmp : nullptr;
+  a.status = &p.ctrl->status;
+  a.tile_seg = reinterpret_cast<int64_t *>(t + l.tile_seg);
+  a.desc = t + l.desc;
+  a.max_tiles = l.max_tiles;
+  for (int k = 1; k <= levels && k <= seg::MAXLV; ++k) {
+    a.k = k;
+    a.count = &p.ctrl->lvl_count[k];
+    rc = launch_segmented_level(a, st);
+    if (rc != NSORT_OK) return rc;
   }
   return NSORT_OK;
 }
