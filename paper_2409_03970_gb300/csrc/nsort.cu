@@ -1592,32 +1592,32 @@ __device__ __forceinline__ int ceil_log2_i64(int64_t x) {
   return p;
 }
 
+// Grid-stride over the segments; nothing to do (and an immediate return)
+// when the offsets were malformed or no segment has k levels.
 __global__ void seg_describe_kernel(const int64_t *__restrict__ off, int64_t nseg,
                                     int64_t min_len, int tile, int k, int mt,
-                                    const int *status, unsigned long long *count,
-                                    int64_t *__restrict__ tile_seg) {
+                                    const int *status, const int *max_level,
+                                    unsigned long long *count, int64_t *__restrict__ tile_seg) {
   pdl_wait();      // the previous kernel of the stream has finished writing
-  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= nseg || *status != NSORT_OK) return;
-  const int64_t L = off[s + 1] - off[s];
-  if (L <= min_len || ceil_log2_i64((L + tile - 1) / tile) < k) return;
+  if (*status != NSORT_OK || *max_level < k) return;
   const int64_t run = (int64_t)tile << (k - 1);
   const int64_t tpp = (2 * run + mt - 1) / mt;
-  const int64_t full = L / (2 * run);
-  const int64_t tiles = full * tpp + (L - full * 2 * run + mt - 1) / mt;
-  const int64_t base = (int64_t)atomicAdd(count, (unsigned long long)tiles);
-  for (int64_t j = 0; j < tiles; ++j) tile_seg[base + j] = (s << 32) | j;
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < nseg;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t L = off[s + 1] - off[s];
+    if (L <= min_len || ceil_log2_i64((L + tile - 1) / tile) < k) continue;
+    const int64_t full = L / (2 * run);
+    const int64_t tiles = full * tpp + (L - full * 2 * run + mt - 1) / mt;
+    const int64_t base = (int64_t)atomicAdd(count, (unsigned long long)tiles);
+    for (int64_t j = 0; j < tiles; ++j) tile_seg[base + j] = (s << 32) | j;
+  }
 }
 
+// Descriptor of merge tile (segment, tile in segment) = e of level k.
 template <typename K>
-__global__ void seg_partition_kernel(const int64_t *__restrict__ off, int tile, int k, int mt,
-                                     const unsigned long long *count,
-                                     const int64_t *__restrict__ tile_seg,
-                                     const K *buf0, const K *buf1, PairTile *__restrict__ desc) {
-  pdl_wait();      // the previous kernel of the stream has finished writing
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)*count) return;
-  const int64_t e = tile_seg[t];
+__device__ __forceinline__ void seg_partition_tile(const int64_t *__restrict__ off, int tile,
+                                                   int k, int mt, int64_t e, const K *buf0,
+                                                   const K *buf1, PairTile *out) {
   const int64_t sid = e >> 32, j = e & 0xFFFFFFFFll;
   const int64_t o = off[sid];
   const int64_t L = off[sid + 1] - o;
@@ -1645,7 +1645,19 @@ __global__ void seg_partition_kernel(const int64_t *__restrict__ off, int tile, 
   g.count = (int)(d1 - d0);
   g.nb = g.count - g.na;
   g.flags = in1 | (k == P ? 2 : 0);
-  desc[t] = g;
+  *out = g;
+}
+
+template <typename K>
+__global__ void seg_partition_kernel(const int64_t *__restrict__ off, int tile, int k, int mt,
+                                     const unsigned long long *count,
+                                     const int64_t *__restrict__ tile_seg,
+                                     const K *buf0, const K *buf1, PairTile *__restrict__ desc) {
+  pdl_wait();      // the previous kernel of the stream has finished writing
+  const int64_t ntiles = (int64_t)*count;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ntiles;
+       t += (int64_t)gridDim.x * blockDim.x)
+    seg_partition_tile(off, tile, k, mt, tile_seg[t], buf0, buf1, desc + t);
 }
 
 template <bool PAIRS>
@@ -1678,12 +1690,15 @@ int launch_segmented_level(const SegLevelArgs &a, cudaStream_t st) {
   const int mt = seg_merge_tile(pairs);
   {
     TraceScope tr(TK_SEG_BIN, st);
-    launch_pdl(seg_describe_kernel, (unsigned)((a.nseg + 255) / 256), 256, 0, st, a.off, a.nseg,
-               a.min_len, a.tile, a.k, mt, (const int *)a.status, a.count, a.tile_seg);
+    const int64_t blocks = (a.nseg + 255) / 256;
+    launch_pdl(seg_describe_kernel, (unsigned)(blocks < 1024 ? blocks : 1024), 256, 0, st, a.off,
+               a.nseg, a.min_len, a.tile, a.k, mt, (const int *)a.status, a.max_level, a.count,
+               a.tile_seg);
   }
   {
     TraceScope tr(TK_PARTITION, st);
-    launch_pdl(seg_partition_kernel<uint32_t>, (unsigned)((a.max_tiles + 255) / 256), 256, 0, st,
+    const int64_t blocks = (a.max_tiles + 255) / 256;
+    launch_pdl(seg_partition_kernel<uint32_t>, (unsigned)(blocks < 1024 ? blocks : 1024), 256, 0, st,
                a.off, a.tile, a.k, mt, (const unsigned long long *)a.count,
                (const int64_t *)a.tile_seg, (const uint32_t *)a.kout, (const uint32_t *)a.ktmp,
                static_cast<PairTile *>(a.desc));

@@ -54,11 +54,18 @@ struct SegLevelArgs {
   uint32_t *kout, *ktmp;
   uint32_t *vout, *vtmp;       // both null for keys only
   int *status;                 // device status word (NSORT_OK: offsets are valid)
+  const int *max_level;        // device: the most merge levels any segment of the batch needs
   unsigned long long *count;   // device counter of this level's tiles, zero before the call
   int64_t *tile_seg;           // device scratch, max_tiles entries
   void *desc;                  // device scratch, max_tiles descriptors
   int64_t max_tiles;
 };
+// nsort_segmented for a caller that knows no segment is longer than
+// max_seg_len keys (the server's co-batches): only the merge levels such a
+// segment needs are launched.
+int segmented_impl(const void *d_keys_in, void *d_keys_out, const uint32_t *d_vals_in,
+                   uint32_t *d_vals_out, const int64_t *d_offsets, uint64_t nseg, uint64_t n,
+                   int dtype, void *d_tmp, size_t tmp_bytes, void *stream, uint64_t max_seg_len);
 int seg_merge_tile(bool pairs);
 size_t seg_tile_desc_bytes();
 int launch_segmented_level(const SegLevelArgs &a, cudaStream_t st);

@@ -500,10 +500,11 @@ extern "C" int nsort_segmented_get_config(nsort_seg_config *cfg) {
   return NSORT_OK;
 }
 
-extern "C" int nsort_segmented(const void *d_keys_in, void *d_keys_out, const uint32_t *d_vals_in,
-                               uint32_t *d_vals_out, const int64_t *d_offsets, uint64_t nseg,
-                               uint64_t n, int dtype, void *d_tmp, size_t tmp_bytes,
-                               void *stream) {
+namespace nsort {
+
+int segmented_impl(const void *d_keys_in, void *d_keys_out, const uint32_t *d_vals_in,
+                   uint32_t *d_vals_out, const int64_t *d_offsets, uint64_t nseg, uint64_t n,
+                   int dtype, void *d_tmp, size_t tmp_bytes, void *stream, uint64_t max_seg_len) {
   if (dtype != NSORT_U32 && dtype != NSORT_I32 && dtype != NSORT_F32) return NSORT_EINVAL;
   if (n > MAX_KEYS || nseg >= (uint64_t(1) << 31)) return NSORT_EINVAL;
   if ((d_vals_in == nullptr) != (d_vals_out == nullptr)) return NSORT_EINVAL;
@@ -569,10 +570,11 @@ extern "C" int nsort_segmented(const void *d_keys_in, void *d_keys_out, const ui
     set_last_error(std::string("nsort_segmented: ") + cudaGetErrorString(e));
     return NSORT_ECUDA;
   }
-  // the merge levels: as many as a segment of all n keys would need (the
-  // host does not know the batch's longest segment; later levels find no
-  // tiles)
-  const int64_t tiles0 = ((int64_t)n + p.tile - 1) / p.tile;
+  // the merge levels: as many as a segment of max_seg_len keys would need
+  // (the host does not know the batch's longest segment; later levels find
+  // no tiles)
+  const uint64_t longest = max_seg_len < n ? max_seg_len : n;
+  const int64_t tiles0 = ((int64_t)longest + p.tile - 1) / p.tile;
   int levels = 0;
   while ((int64_t(1) << levels) < tiles0) ++levels;
   SegLevelArgs a;
@@ -587,6 +589,7 @@ extern "C" int nsort_segmented(const void *d_keys_in, void *d_keys_out, const ui
   a.vout = pairs ? p.vout : nullptr;
   a.vtmp = pairs ? p.vtmp : nullptr;
   a.status = &p.ctrl->status;
+  a.max_level = &p.ctrl->max_level;
   a.tile_seg = reinterpret_cast<int64_t *>(t + l.tile_seg);
   a.desc = t + l.desc;
   a.max_tiles = l.max_tiles;
@@ -597,5 +600,15 @@ extern "C" int nsort_segmented(const void *d_keys_in, void *d_keys_out, const ui
     if (rc != NSORT_OK) return rc;
   }
   return NSORT_OK;
+}
+
+}  // namespace nsort
+
+extern "C" int nsort_segmented(const void *d_keys_in, void *d_keys_out, const uint32_t *d_vals_in,
+                               uint32_t *d_vals_out, const int64_t *d_offsets, uint64_t nseg,
+                               uint64_t n, int dtype, void *d_tmp, size_t tmp_bytes,
+                               void *stream) {
+  return segmented_impl(d_keys_in, d_keys_out, d_vals_in, d_vals_out, d_offsets, nseg, n, dtype,
+                        d_tmp, tmp_bytes, stream, n);
 }
 

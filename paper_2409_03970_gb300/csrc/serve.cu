@@ -178,8 +178,11 @@ void launch(Ctx *c, int s, std::vector<Pending> &picked, std::vector<std::pair<s
     const int kind = picked[0].kind;
     const bool pairs = kind == NSORT_KIND_PAIRS;
     const size_t count = picked.size();
-    uint64_t total = 0;
-    for (auto &p : picked) total += p.n;
+    uint64_t total = 0, longest = 0;
+    for (auto &p : picked) {
+      total += p.n;
+      longest = p.n > longest ? p.n : longest;
+    }
     char *base = c->arena_base + allocs[0].first;
     size_t o = 0;
     uint32_t *sk = reinterpret_cast<uint32_t *>(base + o);
@@ -216,8 +219,10 @@ void launch(Ctx *c, int s, std::vector<Pending> &picked, std::vector<std::pair<s
     if (rc == NSORT_OK) {
       const unsigned g = (unsigned)(count < 2048 ? count : 2048);
       batch_gather_kernel<<<g, 256, 0, slot.stream>>>(items, (int)count, sk, sv);
-      rc = nsort_segmented(sk, sk, sv, sv, offs, count, total, picked[0].dtype, segtmp, segbytes,
-                           slot.stream);
+      // no segment is longer than the longest request: launch only the
+      // merge levels it needs
+      rc = segmented_impl(sk, sk, sv, sv, offs, count, total, picked[0].dtype, segtmp, segbytes,
+                          slot.stream, longest);
       if (rc == NSORT_OK) {
         batch_scatter_kernel<<<g, 256, 0, slot.stream>>>(items, (int)count, sk, sv);
         if (cudaGetLastError() != cudaSuccess) rc = NSORT_ECUDA;
