@@ -185,8 +185,10 @@ def source_hash(files):
 
 
 def load_traffic(kernel: str):
-    """Per-key DRAM bytes of `kernel` from the committed ncu summary, or None
-    when the kernel's sources changed since the counters were taken."""
+    """DRAM bytes read and written by one launch of `kernel`, from the
+    committed ncu capture (profiles/traffic.json: captured_n, read_bytes,
+    write_bytes), or None when the kernel's sources changed since the
+    counters were taken."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -904,10 +906,15 @@ def main():
         per_launch_ms = mk["total_ms"] / mk["launches"]
         achieved = 2 * esize * n / (per_launch_ms / 1e3) / 1e9
         tr = load_traffic(mk_name)
+        # the counters of one launch at this very workload size, else nothing
+        # (no scaling from another size)
+        tr = tr if tr and tr["captured_n"] == n else None
         roofline = {"bound": "hbm", "kernel": mk_name, "achieved": achieved,
                     "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
                     "peak_source": peaks["source"],
-                    "traffic": (tr["bytes_per_key"] * n) if tr else None,
+                    "traffic": (tr["read_bytes"] + tr["write_bytes"]) if tr else None,
+                    "traffic_read": tr["read_bytes"] if tr else None,
+                    "traffic_write": tr["write_bytes"] if tr else None,
                     "algorithmic_bytes": 2 * esize * n, "launch_ms": per_launch_ms,
                     "share_of_step": mk["total_ms"] / (traced_ms * args.steps),
                     "timing": "launch durations from a traced repeat of the timed steps "

@@ -35,13 +35,16 @@ def test_peak_from_measured_file_else_fallback(bench, tmp_path, monkeypatch):
 
 
 def test_committed_traffic_is_plausible(bench):
-    """Each committed figure is DRAM bytes per key of one merge pass: above
-    zero and at most the algorithmic read + write (plus a few percent).  It
-    names the profile it came from and the sources its hash covers."""
+    """Each committed figure is the DRAM bytes read and written by one merge
+    launch at the n it was captured at: each at most the algorithmic read
+    (or write) of that n plus a few percent, and above zero.  It names the
+    profile it came from and the sources its hash covers."""
     d = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-    for kernel, word in (("merge_keys", 4), ("merge_keys64", 8)):
+    for kernel, word in (("merge_keys", 4),):
         t = d[kernel]
-        assert 0 < t["bytes_per_key"] <= 2 * word * 1.05
+        n = t["captured_n"]
+        assert 0 < t["read_bytes"] <= word * n * 1.05
+        assert 0 < t["write_bytes"] <= word * n * 1.05
         assert os.path.exists(os.path.join(ROOT, t["profile"]))
         assert all(os.path.exists(os.path.join(ROOT, f)) for f in t["sources"])
 
@@ -51,10 +54,10 @@ def test_traffic_goes_null_when_a_source_changes(bench, tmp_path, monkeypatch):
     src.write_text("// version 1\n")
     (tmp_path / "profiles").mkdir()
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    entry = {"bytes_per_key": 7.2, "sources": ["kernel.cu"],
-             "source_sha": bench.source_hash(["kernel.cu"])}
+    entry = {"captured_n": 1 << 28, "read_bytes": 1 << 30, "write_bytes": 1 << 30,
+             "sources": ["kernel.cu"], "source_sha": bench.source_hash(["kernel.cu"])}
     (tmp_path / "profiles" / "traffic.json").write_text(json.dumps({"merge_keys": entry}))
-    assert bench.load_traffic("merge_keys")["bytes_per_key"] == 7.2
+    assert bench.load_traffic("merge_keys")["read_bytes"] == 1 << 30
     assert bench.load_traffic("merge_pairs") is None
     src.write_text("// version 2\n")
     assert bench.load_traffic("merge_keys") is None
