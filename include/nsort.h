@@ -67,7 +67,8 @@ typedef enum {
     NSORT_KIND_SEGMENTED = 2,       /* nsort_segmented, keys only */
     NSORT_KIND_SEGMENTED_PAIRS = 3, /* nsort_segmented with values */
     NSORT_KIND_MERGE = 4,           /* nsort_merge_shards, keys only (nseg = number of runs) */
-    NSORT_KIND_MERGE_PAIRS = 5      /* nsort_merge_shards with values */
+    NSORT_KIND_MERGE_PAIRS = 5,     /* nsort_merge_shards with values */
+    NSORT_KIND_PAIRS64 = 6          /* nsort_pairs64 */
 } nsort_kind;
 
 typedef enum {
@@ -127,6 +128,21 @@ int nsort_keys(const void *d_keys_in, void *d_keys_out, uint64_t n, int dtype,
 int nsort_pairs(const void *d_keys_in, const uint32_t *d_vals_in,
                 void *d_keys_out, uint32_t *d_vals_out, uint64_t n, int dtype,
                 void *d_tmp, size_t tmp_bytes, void *stream);
+
+/* Stable key/value sort with 64-bit payloads (row ids, pointers, ...):
+ * 32-bit keys of dtype U32 / I32 / F32 as in nsort_pairs, each carrying a
+ * 64-bit payload that moves with its key.  Equal keys keep their input
+ * order.  d_vals_in / d_vals_out: n uint64, 8-byte aligned; d_keys_out
+ * and d_vals_out must be 16-byte aligned (the merge passes move them with
+ * bulk copies).  In place (in == out) is allowed.  Scratch:
+ * nsort_temp_bytes(NSORT_KIND_PAIRS64, n, 0, dtype).  Errors as
+ * nsort_pairs, plus NSORT_EINVAL for a misaligned payload or output.
+ * Paper: the sort of Sec. 2.1 with a wider payload word (the register
+ * width depends on the element type, Sec. 2.2); the payload width is this
+ * library's extension. */
+int nsort_pairs64(const void *d_keys_in, const uint64_t *d_vals_in, void *d_keys_out,
+                  uint64_t *d_vals_out, uint64_t n, int dtype, void *d_tmp, size_t tmp_bytes,
+                  void *stream);
 
 /* Segmented sort: nseg independent arrays stored back to back.  d_offsets
  * is a DEVICE array of nseg+1 int64 (CSR form): segment s is

@@ -129,24 +129,28 @@ __global__ void __launch_bounds__(NT) tile_sort_keys_kernel(const uint32_t *in, 
 
 // Tile sort, key/value pairs.  The networks sort 64-bit composites
 // (key << 32 | position in tile); positions make every composite distinct,
-// so the network's result is the stable order.  Values are staged in shared
-// memory and gathered by position at the end.
-template <int NT, int DT, bool FINAL>
+// so the network's result is the stable order.  32-bit values (V) are
+// staged in shared memory and gathered by position at the end; 64-bit ones
+// are gathered by position from global memory, all of them before the
+// first store (in == out is allowed).
+template <int NT, int DT, bool FINAL, typename V = uint32_t>
 __global__ void __launch_bounds__(NT, 2) tile_sort_pairs_kernel(const uint32_t *kin,
-                                                             const uint32_t *vin,
-                                                             uint32_t *kout, uint32_t *vout,
-                                                             int64_t n, uint32_t *samp) {
+                                                             const V *vin, uint32_t *kout,
+                                                             V *vout, int64_t n, uint32_t *samp) {
   constexpr int TILE = NT * 16;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   uint64_t *s = reinterpret_cast<uint64_t *>(smem_raw);
-  uint32_t *sv = reinterpret_cast<uint32_t *>(s + merge_smem_len<uint64_t>(NT * 16, 16));
+  [[maybe_unused]] uint32_t *sv =
+      reinterpret_cast<uint32_t *>(s + merge_smem_len<uint64_t>(NT * 16, 16));
   const int tid = threadIdx.x;
   const int64_t base = (int64_t)blockIdx.x * TILE;
   const int count = (int)(n - base < TILE ? n - base : TILE);
+  if constexpr (sizeof(V) == 4) {
 #pragma unroll
-  for (int j = 0; j < 16; ++j) {
-    const int e = tid + NT * j;
-    if (e < count) sv[pidx<uint32_t>(e)] = vin[base + e];
+    for (int j = 0; j < 16; ++j) {
+      const int e = tid + NT * j;
+      if (e < count) sv[pidx<uint32_t>(e)] = vin[base + e];
+    }
   }
   uint64_t r[16];
 #pragma unroll
@@ -160,15 +164,33 @@ __global__ void __launch_bounds__(NT, 2) tile_sort_pairs_kernel(const uint32_t *
   }
   sort_tile_in_block<NT, 16, Green16Columns, uint64_t, false>(r, s);
   // every thread passed a barrier after the values were staged
-  uint32_t ko[16], vo[16];
-#pragma unroll
-  for (int k = 0; k < 16; ++k) {
-    ko[k] = (uint32_t)(r[k] >> 32);
-    vo[k] = sv[pidx<uint32_t>((int)(r[k] & 0xFFFFu) & (TILE - 1))];
-  }
   const bool full = count == TILE && aligned16(kout + base) && aligned16(vout + base);
-  store_run<16, FINAL ? DT : DT_U32>(ko, kout + base, count, full);
-  store_run<16, DT_U32>(vo, vout + base, count, full);
+  uint32_t ko[16];
+  if constexpr (sizeof(V) == 4) {
+    V vo[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      ko[k] = (uint32_t)(r[k] >> 32);
+      vo[k] = sv[pidx<uint32_t>((int)(r[k] & 0xFFFFu) & (TILE - 1))];
+    }
+    store_run<16, FINAL ? DT : DT_U32>(ko, kout + base, count, full);
+    store_run<16, DT_U32>(vo, vout + base, count, full);
+  } else {
+    // keys first (every key was read before the block merges' barriers),
+    // then the payloads by position, all read before any is written
+    int pos[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      ko[k] = (uint32_t)(r[k] >> 32);
+      pos[k] = (int)(r[k] & 0xFFFFu) & (TILE - 1);
+    }
+    store_run<16, FINAL ? DT : DT_U32>(ko, kout + base, count, full);
+    V vo[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) vo[k] = tid * 16 + k < count ? vin[base + pos[k]] : V(0);
+    __syncthreads();
+    store_run<16, DT_U32>(vo, vout + base, count, full);
+  }
   if (!FINAL && samp && !(tid & (SAMPLE / 16 - 1)) && tid * 16 < count)
     store_keep_in_l2(samp + (base + tid * 16) / SAMPLE, ko[0]);
 }
@@ -578,10 +600,9 @@ __device__ __forceinline__ SmemSlices smem_slices(const PairTile &g) {
 // windows are clipped at n_al = n rounded down to a multiple of EPV, past
 // which the warps load the at most EPV - 1 remaining elements themselves.
 // Values (pairs, 32-bit keys only) are 32-bit words at the keys' offsets.
-template <typename K>
-__device__ __forceinline__ void issue_tile(const K *__restrict__ src,
-                                           const uint32_t *__restrict__ vsrc, int64_t n_al,
-                                           const PairTile &g, K *buf, uint32_t *vbuf,
+template <typename K, typename V = uint32_t>
+__device__ __forceinline__ void issue_tile(const K *__restrict__ src, const V *__restrict__ vsrc,
+                                           int64_t n_al, const PairTile &g, K *buf, V *vbuf,
                                            uint64_t *bar) {
   constexpr int64_t EPV = 16 / sizeof(K);
   const SmemSlices l = smem_slices<K>(g);
@@ -595,8 +616,11 @@ __device__ __forceinline__ void issue_tile(const K *__restrict__ src,
       (g.na > 0 && aw1 > aw0) ? (uint32_t)((aw1 - aw0) * (int64_t)sizeof(K)) : 0u;
   const uint32_t bytes_b =
       (g.nb > 0 && bw1 > bw0) ? (uint32_t)((bw1 - bw0) * (int64_t)sizeof(K)) : 0u;
-  const uint32_t vbytes_a = vsrc ? bytes_a / (uint32_t)(sizeof(K) / 4) : 0u;
-  const uint32_t vbytes_b = vsrc ? bytes_b / (uint32_t)(sizeof(K) / 4) : 0u;
+  // values sit at the keys' element offsets, so a window holds as many
+  // values as keys (16-byte aligned as long as a value is not narrower
+  // than a key, which the merge kernel checks for pairs)
+  const uint32_t vbytes_a = vsrc ? (uint32_t)((uint64_t)bytes_a * sizeof(V) / sizeof(K)) : 0u;
+  const uint32_t vbytes_b = vsrc ? (uint32_t)((uint64_t)bytes_b * sizeof(V) / sizeof(K)) : 0u;
   mbar_arrive_expect_tx(bar, bytes_a + bytes_b + vbytes_a + vbytes_b);
   if (bytes_a) bulk_load(buf, src + aw0, bytes_a, bar);
   if (bytes_b) bulk_load(buf + l.base_b, src + bw0, bytes_b, bar);
@@ -629,11 +653,12 @@ __device__ __forceinline__ void issue_tile(const K *__restrict__ src,
 // TableRuns for merging runs of any lengths; the latter also maps keys from
 // bit patterns on arrival and back on the way out, by its run-time dtypes,
 // in place of DT_OUT).
+// V: the payload word of pairs (32- or 64-bit).
 template <int NT, int VT, int DT_OUT, bool PAIRS, typename K = uint32_t, bool SELF = false,
-          class GEOM = UniformRuns>
+          class GEOM = UniformRuns, typename V = uint32_t>
 __global__ void __launch_bounds__(NT, PAIRS ? 3 : 4) merge_tma_kernel(
-    const K *__restrict__ src, const uint32_t *__restrict__ vsrc, K *__restrict__ dst,
-    uint32_t *__restrict__ vdst, int64_t n, const GEOM geom, int64_t num_tiles_arg,
+    const K *__restrict__ src, const V *__restrict__ vsrc, K *__restrict__ dst,
+    V *__restrict__ vdst, int64_t n, const GEOM geom, int64_t num_tiles_arg,
     const int64_t *__restrict__ split, int *status, K *samp, int reverse) {
   pdl_wait();      // the previous kernel of the stream has finished writing
   int64_t num_tiles = num_tiles_arg;
@@ -652,14 +677,14 @@ __global__ void __launch_bounds__(NT, PAIRS ? 3 : 4) merge_tma_kernel(
   static_assert(WOUT % 4 == 0, "warp output slices must be 16-byte multiples");
   static_assert(WOUT <= 32 * SAMPLE, "one sample per lane and warp slice");
   static_assert(!PAIRS || sizeof(K) == 4, "pairs carry 32-bit keys");
+  static_assert(!PAIRS || sizeof(V) >= sizeof(K), "value windows stay 16-byte aligned");
   // dynamic shared memory: keys [in 0][in 1] | values [in 0][in 1] | keys out | values out
   extern __shared__ __align__(128) unsigned char tma_smem[];
   K(*in_buf)[IN_LEN] = reinterpret_cast<K(*)[IN_LEN]>(tma_smem);
-  uint32_t(*vin_buf)[IN_LEN] = reinterpret_cast<uint32_t(*)[IN_LEN]>(
-      tma_smem + (PAIRS ? 2 * IN_LEN * sizeof(K) : 0));
-  K *out_buf = reinterpret_cast<K *>(tma_smem + (PAIRS ? 2 * IN_LEN * (sizeof(K) + 4)
+  V(*vin_buf)[IN_LEN] = reinterpret_cast<V(*)[IN_LEN]>(tma_smem + (PAIRS ? 2 * IN_LEN * sizeof(K) : 0));
+  K *out_buf = reinterpret_cast<K *>(tma_smem + (PAIRS ? 2 * IN_LEN * (sizeof(K) + sizeof(V))
                                                         : 2 * IN_LEN * sizeof(K)));
-  uint32_t *vout_buf = reinterpret_cast<uint32_t *>(out_buf + (NT / 32) * WSTRIDE);
+  V *vout_buf = reinterpret_cast<V *>(out_buf + (NT / 32) * WSTRIDE);
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ PairTile desc[2];   // geometry of the tile in each buffer, written by thread 0
   const int tid = threadIdx.x;
@@ -673,7 +698,7 @@ __global__ void __launch_bounds__(NT, PAIRS ? 3 : 4) merge_tma_kernel(
     if constexpr (GEOM::kDesc) return (g.flags & 1) ? geom.buf1 : geom.buf0;
     else return src;
   };
-  auto vsrc_of = [&](const PairTile &g) -> const uint32_t * {
+  auto vsrc_of = [&](const PairTile &g) -> const V * {
     if constexpr (GEOM::kDesc) return (g.flags & 1) ? geom.vbuf1 : geom.vbuf0;
     else return vsrc;
   };
@@ -681,7 +706,7 @@ __global__ void __launch_bounds__(NT, PAIRS ? 3 : 4) merge_tma_kernel(
     if constexpr (GEOM::kDesc) return (g.flags & 1) ? geom.buf0 : geom.buf1;
     else return dst;
   };
-  auto vdst_of = [&](const PairTile &g) -> uint32_t * {
+  auto vdst_of = [&](const PairTile &g) -> V * {
     if constexpr (GEOM::kDesc) return (g.flags & 1) ? geom.vbuf0 : geom.vbuf1;
     else return vdst;
   };
@@ -738,7 +763,7 @@ __global__ void __launch_bounds__(NT, PAIRS ? 3 : 4) merge_tma_kernel(
   __syncthreads();
   bool ok = true;
   K *wout = out_buf + warp * WSTRIDE;
-  uint32_t *wvout = vout_buf + warp * WSTRIDE;
+  V *wvout = vout_buf + warp * WSTRIDE;
   for (int it = 0; t < num_tiles; ++it, t += G) {
     const int b = it & 1;
     const int64_t tn = t + G;
@@ -770,12 +795,12 @@ __global__ void __launch_bounds__(NT, PAIRS ? 3 : 4) merge_tma_kernel(
     }
     const PairTile g = desc[b];
     const K *tsrc = ksrc_of(g);
-    const uint32_t *tvsrc = vsrc_of(g);
+    const V *tvsrc = vsrc_of(g);
     K *tdst = kdst_of(g);
-    uint32_t *tvdst = vdst_of(g);
+    V *tvdst = vdst_of(g);
     const SmemSlices l = smem_slices<K>(g);
     K *s = in_buf[b];
-    uint32_t *sv = vin_buf[b];
+    V *sv = vin_buf[b];
     const int a0 = l.sh_a, b0 = l.base_b + l.sh_b;
     if constexpr (GEOM::kMaps) {
       if (geom.dt_in != DT_U32 && geom.dt_in != DT_U64) {   // the same in every thread
@@ -818,7 +843,7 @@ __global__ void __launch_bounds__(NT, PAIRS ? 3 : 4) merge_tma_kernel(
     int from[VT];
     if (PAIRS) serial_merge_plain<VT, true>(s, a0 + ai, a0 + g.na, b0 + diag - ai, b0 + g.nb, o, from);
     else serial_merge_sentinel<VT>(s, a0 + ai, b0 + diag - ai, o);
-    uint32_t ov[VT];
+    V ov[VT];
     if (PAIRS) {
 #pragma unroll
       for (int k = 0; k < VT; ++k) ov[k] = sv[from[k]];
@@ -830,7 +855,7 @@ __global__ void __launch_bounds__(NT, PAIRS ? 3 : 4) merge_tma_kernel(
     // sh: gb's offset past a 16-byte boundary, 0 for the uniform runs of a sort
     const int sh = GEOM::kAnyStart ? (int)(gb & (EPV - 1)) : 0;
     K *ws = wout + sh;
-    uint32_t *wvs = wvout + sh;
+    V *wvs = wvout + sh;
     if (lane == 0) bulk_wait_read_all();   // the warp's previous stores have left its slices
     __syncwarp();
     int dt_out = DT_OUT;   // a constant unless GEOM maps at run time
@@ -868,7 +893,7 @@ __global__ void __launch_bounds__(NT, PAIRS ? 3 : 4) merge_tma_kernel(
       const int tail = wcount - head - body;
       if (lane == 0 && body) {
         bulk_store(tdst + gb + head, ws + head, (uint32_t)body * (uint32_t)sizeof(K));
-        if (PAIRS) bulk_store(tvdst + gb + head, wvs + head, (uint32_t)body * 4u);
+        if (PAIRS) bulk_store(tvdst + gb + head, wvs + head, (uint32_t)body * (uint32_t)sizeof(V));
         bulk_commit();
       }
       if (lane < head) {
@@ -916,11 +941,12 @@ constexpr int MERGE64_VT = 16;
 
 // dynamic shared memory of merge_tma_kernel: input buffers (two per array)
 // and output staging (one per array); key words of kbytes bytes, 32-bit values
-constexpr size_t tma_merge_smem(int tile, bool pairs, size_t kbytes = 4) {
-  return (kbytes + (pairs ? 4 : 0)) * (2 * ((tile + 2 * 32 + 16) & ~3) + tile);
+constexpr size_t tma_merge_smem(int tile, bool pairs, size_t kbytes = 4, size_t vbytes = 4) {
+  return (kbytes + (pairs ? vbytes : 0)) * (2 * ((tile + 2 * 32 + 16) & ~3) + tile);
 }
 constexpr size_t TMA_MERGE_SMEM = tma_merge_smem(TMA_MERGE_TILE, false);
 constexpr size_t TMA_PMERGE_SMEM = tma_merge_smem(TMA_PMERGE_TILE, true);
+constexpr size_t TMA_PMERGE64_SMEM = tma_merge_smem(TMA_PMERGE_TILE, true, 4, 8);   // 64-bit payloads
 constexpr size_t TMA_K64_SMEM = tma_merge_smem(TMA_K64_TILE, false, 8);
 constexpr int KEYS64_SORT_TILE = KEYS64_SORT_NT * 16;
 constexpr size_t KEYS64_SORT_SMEM =
@@ -937,6 +963,11 @@ constexpr int PMERGE_TILE = PMERGE_NT * PMERGE_VT;
 constexpr size_t PAIRS_SORT_SMEM =
     sizeof(uint64_t) * merge_smem_len<uint64_t>(PAIRS_SORT_TILE, 16) +
     sizeof(uint32_t) * padded_len<uint32_t>(PAIRS_SORT_TILE);
+// 64-bit payloads are gathered from global memory: no value staging
+constexpr size_t PAIRS64_SORT_SMEM = sizeof(uint64_t) * merge_smem_len<uint64_t>(PAIRS_SORT_TILE, 16);
+
+template <typename V>
+constexpr size_t pairs_sort_smem() { return sizeof(V) == 4 ? PAIRS_SORT_SMEM : PAIRS64_SORT_SMEM; }
 
 }  // namespace
 
@@ -950,7 +981,8 @@ int64_t pair_tiles(int64_t n, int64_t run, int tile, int64_t *tpp_out) {
 
 Plan make_plan(int kind, uint64_t n, int dtype) {
   Plan p;
-  const bool pairs = kind == NSORT_KIND_PAIRS;
+  const bool pairs = kind == NSORT_KIND_PAIRS || kind == NSORT_KIND_PAIRS64;
+  const size_t vw = kind == NSORT_KIND_PAIRS64 ? 8 : 4;   // bytes per payload word
   const bool wide = !pairs && dtype >= NSORT_U64;   // 64-bit keys
   const size_t kw = wide ? 8 : 4;                   // bytes per key word
   p.n = (int64_t)n;
@@ -970,7 +1002,7 @@ Plan make_plan(int kind, uint64_t n, int dtype) {
     if (t > max_tiles) max_tiles = t;
   }
   const size_t kb = align_up((size_t)n * kw, 256);
-  const size_t vb = align_up((size_t)n * 4, 256);
+  const size_t vb = align_up((size_t)n * vw, 256);
   p.status_off = 0;
   p.keys_off = 256;
   p.vals_off = p.keys_off + kb;
@@ -1084,35 +1116,38 @@ static void launch_merge_keys(const uint32_t *src, uint32_t *dst, int64_t n, int
 #undef NSORT_MK
 }
 
-template <int DT, bool FIN>
+template <int DT, bool FIN, typename V>
 static cudaError_t pairs_smem_attr() {
-  return cudaFuncSetAttribute(tile_sort_pairs_kernel<PAIRS_SORT_NT, DT, FIN>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PAIRS_SORT_SMEM);
+  return cudaFuncSetAttribute(tile_sort_pairs_kernel<PAIRS_SORT_NT, DT, FIN, V>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)pairs_sort_smem<V>());
 }
 
+template <typename V>
 static int ensure_pairs_smem_attr() {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return launch_status("cudaGetDevice");
   static std::atomic<uint64_t> done_mask{0};
   const uint64_t bit = dev < 64 ? (uint64_t(1) << dev) : 0;
   if (bit && (done_mask.load() & bit)) return NSORT_OK;
-  cudaError_t e = pairs_smem_attr<DT_U32, false>();
-  if (e == cudaSuccess) e = pairs_smem_attr<DT_U32, true>();
-  if (e == cudaSuccess) e = pairs_smem_attr<DT_I32, false>();
-  if (e == cudaSuccess) e = pairs_smem_attr<DT_I32, true>();
-  if (e == cudaSuccess) e = pairs_smem_attr<DT_F32, false>();
-  if (e == cudaSuccess) e = pairs_smem_attr<DT_F32, true>();
+  cudaError_t e = pairs_smem_attr<DT_U32, false, V>();
+  if (e == cudaSuccess) e = pairs_smem_attr<DT_U32, true, V>();
+  if (e == cudaSuccess) e = pairs_smem_attr<DT_I32, false, V>();
+  if (e == cudaSuccess) e = pairs_smem_attr<DT_I32, true, V>();
+  if (e == cudaSuccess) e = pairs_smem_attr<DT_F32, false, V>();
+  if (e == cudaSuccess) e = pairs_smem_attr<DT_F32, true, V>();
   if (e != cudaSuccess) return launch_status("cudaFuncSetAttribute");
   done_mask.fetch_or(bit);
   return NSORT_OK;
 }
 
-static void launch_tile_sort_pairs(const uint32_t *kin, const uint32_t *vin, uint32_t *kout,
-                                   uint32_t *vout, int64_t n, int dt, bool final_pass,
-                                   unsigned grid, uint32_t *samp, cudaStream_t st) {
-#define NSORT_TSP(DT, FIN)                                                      \
-  tile_sort_pairs_kernel<PAIRS_SORT_NT, DT, FIN><<<grid, PAIRS_SORT_NT, PAIRS_SORT_SMEM, st>>>( \
-      kin, vin, kout, vout, n, samp)
+template <typename V>
+static void launch_tile_sort_pairs(const uint32_t *kin, const V *vin, uint32_t *kout, V *vout,
+                                   int64_t n, int dt, bool final_pass, unsigned grid,
+                                   uint32_t *samp, cudaStream_t st) {
+#define NSORT_TSP(DT, FIN)                                                                  \
+  tile_sort_pairs_kernel<PAIRS_SORT_NT, DT, FIN, V><<<grid, PAIRS_SORT_NT, pairs_sort_smem<V>(), \
+                                                      st>>>(kin, vin, kout, vout, n, samp)
   if (dt == DT_U32) { if (final_pass) NSORT_TSP(DT_U32, true); else NSORT_TSP(DT_U32, false); }
   else if (dt == DT_I32) { if (final_pass) NSORT_TSP(DT_I32, true); else NSORT_TSP(DT_I32, false); }
   else { if (final_pass) NSORT_TSP(DT_F32, true); else NSORT_TSP(DT_F32, false); }
@@ -1136,14 +1171,15 @@ static void launch_partition(const uint32_t *src, int64_t n, int64_t run, const 
   partition_kernel<<<blocks, 256, 0, st>>>(src, n, run, tile, p.num_merge_tiles, split);
 }
 
-template <int NT, int VT, bool PAIRS>
+template <int NT, int VT, bool PAIRS, typename V = uint32_t>
 static void tma_merge_attrs(size_t smem) {
-  const void *fns[6] = {(const void *)merge_tma_kernel<NT, VT, DT_U32, PAIRS>,
-                        (const void *)merge_tma_kernel<NT, VT, DT_I32, PAIRS>,
-                        (const void *)merge_tma_kernel<NT, VT, DT_F32, PAIRS>,
-                        (const void *)merge_tma_kernel<NT, VT, DT_U32, PAIRS, uint32_t, true>,
-                        (const void *)merge_tma_kernel<NT, VT, DT_I32, PAIRS, uint32_t, true>,
-                        (const void *)merge_tma_kernel<NT, VT, DT_F32, PAIRS, uint32_t, true>};
+  using U = UniformRuns;
+  const void *fns[6] = {(const void *)merge_tma_kernel<NT, VT, DT_U32, PAIRS, uint32_t, false, U, V>,
+                        (const void *)merge_tma_kernel<NT, VT, DT_I32, PAIRS, uint32_t, false, U, V>,
+                        (const void *)merge_tma_kernel<NT, VT, DT_F32, PAIRS, uint32_t, false, U, V>,
+                        (const void *)merge_tma_kernel<NT, VT, DT_U32, PAIRS, uint32_t, true, U, V>,
+                        (const void *)merge_tma_kernel<NT, VT, DT_I32, PAIRS, uint32_t, true, U, V>,
+                        (const void *)merge_tma_kernel<NT, VT, DT_F32, PAIRS, uint32_t, true, U, V>};
   for (const void *f : fns) {   // opt in to the dynamic shared memory; prefer it over L1
     cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
@@ -1151,9 +1187,9 @@ static void tma_merge_attrs(size_t smem) {
 }
 
 // Persistent merge pass: SMs x resident CTAs, found once per device and
-// kind (0 keys, 1 pairs, 2 64-bit keys).
+// kind (0 keys, 1 pairs, 2 64-bit keys, 3 pairs with 64-bit payloads).
 static int tma_merge_grid(int64_t tiles, int kind) {
-  static std::atomic<int> cached[3][64];
+  static std::atomic<int> cached[4][64];
   int dev = 0;
   cudaGetDevice(&dev);
   int g = dev < 64 ? cached[kind][dev].load() : 0;
@@ -1175,6 +1211,12 @@ static int tma_merge_grid(int64_t tiles, int kind) {
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(
           &occ, merge_tma_kernel<TMA_K64_NT, TMA_K64_VT, DT_U64, false, uint64_t>, TMA_K64_NT,
           TMA_K64_SMEM);
+    } else if (kind == 3) {
+      tma_merge_attrs<TMA_PMERGE_NT, TMA_PMERGE_VT, true, uint64_t>(TMA_PMERGE64_SMEM);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &occ, merge_tma_kernel<TMA_PMERGE_NT, TMA_PMERGE_VT, DT_U32, true, uint32_t, false,
+                                 UniformRuns, uint64_t>,
+          TMA_PMERGE_NT, TMA_PMERGE64_SMEM);
     } else if (kind == 1) {
       tma_merge_attrs<TMA_PMERGE_NT, TMA_PMERGE_VT, true>(TMA_PMERGE_SMEM);
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(
@@ -1192,18 +1234,21 @@ static int tma_merge_grid(int64_t tiles, int kind) {
   return (int)(tiles < g ? tiles : g);
 }
 
-// One bulk-copy merge pass (keys when vsrc is null, else stable pairs).
+// One bulk-copy merge pass (keys when vsrc is null, else stable pairs with
+// payload word V).
 // samp_in: samples of src (from the previous stage); samp_out: where this
 // pass writes the samples of dst (nullptr for the last pass).
-static void launch_merge_tma(const uint32_t *src, const uint32_t *vsrc, uint32_t *dst,
-                             uint32_t *vdst, int64_t n, int64_t run, int64_t *split, int *status,
-                             int dt_out, const uint32_t *samp_in, uint32_t *samp_out, int reverse,
+template <typename V = uint32_t>
+static void launch_merge_tma(const uint32_t *src, const V *vsrc, uint32_t *dst, V *vdst,
+                             int64_t n, int64_t run, int64_t *split, int *status, int dt_out,
+                             const uint32_t *samp_in, uint32_t *samp_out, int reverse,
                              cudaStream_t st) {
+  constexpr bool V64 = sizeof(V) == 8;
   const bool pairs = vsrc != nullptr;
   const int tile = pairs ? TMA_PMERGE_TILE : TMA_MERGE_TILE;
   int64_t tpp = 0;
   const int64_t tiles = pair_tiles(n, run, tile, &tpp);
-  const unsigned grid = (unsigned)tma_merge_grid(tiles, pairs ? 1 : 0);
+  const unsigned grid = (unsigned)tma_merge_grid(tiles, pairs ? (V64 ? 3 : 1) : 0);
   const UniformRuns geom{n, run, tpp};
   if (tiles > 2 * (int64_t)grid) {
     TraceScope tr(TK_PARTITION, st);
@@ -1213,15 +1258,19 @@ static void launch_merge_tma(const uint32_t *src, const uint32_t *vsrc, uint32_t
     split = nullptr;   // at most two tiles per CTA: each finds its own splitters
   }
   TraceScope tr(pairs ? TK_MERGE_PAIRS : TK_MERGE_KEYS, st);
-#define NSORT_MT1(NT, VT, DT, P, SMEM, SELF)                                                   \
-  launch_pdl(merge_tma_kernel<NT, VT, DT, P, uint32_t, SELF>, grid, NT, SMEM, st, src, vsrc, dst, \
-             vdst, n, geom, tiles, split, status, samp_out, reverse)
+#define NSORT_MT1(NT, VT, DT, P, SMEM, SELF)                                                  \
+  launch_pdl(merge_tma_kernel<NT, VT, DT, P, uint32_t, SELF, UniformRuns, V>, grid, NT, SMEM, st, \
+             src, vsrc, dst, vdst, n, geom, tiles, split, status, samp_out, reverse)
 #define NSORT_MT(NT, VT, DT, P, SMEM)                                                        \
   do {                                                                                       \
     if (split) NSORT_MT1(NT, VT, DT, P, SMEM, false);                                       \
     else NSORT_MT1(NT, VT, DT, P, SMEM, true);                                              \
   } while (0)
-  if (!pairs) {
+  if constexpr (V64) {   // pairs with 64-bit payloads
+    if (dt_out == DT_U32) NSORT_MT(TMA_PMERGE_NT, TMA_PMERGE_VT, DT_U32, true, TMA_PMERGE64_SMEM);
+    else if (dt_out == DT_I32) NSORT_MT(TMA_PMERGE_NT, TMA_PMERGE_VT, DT_I32, true, TMA_PMERGE64_SMEM);
+    else NSORT_MT(TMA_PMERGE_NT, TMA_PMERGE_VT, DT_F32, true, TMA_PMERGE64_SMEM);
+  } else if (!pairs) {
     if (dt_out == DT_U32) NSORT_MT(TMA_MERGE_NT, TMA_MERGE_VT, DT_U32, false, TMA_MERGE_SMEM);
     else if (dt_out == DT_I32) NSORT_MT(TMA_MERGE_NT, TMA_MERGE_VT, DT_I32, false, TMA_MERGE_SMEM);
     else NSORT_MT(TMA_MERGE_NT, TMA_MERGE_VT, DT_F32, false, TMA_MERGE_SMEM);
@@ -1369,8 +1418,9 @@ int sort_keys_impl(const uint32_t *in, uint32_t *out, int64_t n, int dt, void *t
       // the partition reads the samples of this pass's input before the
       // merge overwrites them with the samples of its output
       // the tile sort writes low to high; passes then alternate direction
-      launch_merge_tma(bufs[cur], nullptr, bufs[cur ^ 1], nullptr, n, run, split, status, dt_out,
-                       samp, pass == p.merge_passes - 1 ? nullptr : samp, (pass & 1) == 0, st);
+      launch_merge_tma<uint32_t>(bufs[cur], nullptr, bufs[cur ^ 1], nullptr, n, run, split,
+                                 status, dt_out, samp, pass == p.merge_passes - 1 ? nullptr : samp,
+                                 (pass & 1) == 0, st);
     } else {
       {
         TraceScope tr(TK_PARTITION, st);
@@ -1386,14 +1436,18 @@ int sort_keys_impl(const uint32_t *in, uint32_t *out, int64_t n, int dt, void *t
   return rc;
 }
 
-int sort_pairs_impl(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
-                    int64_t n, int dt, void *tmp, cudaStream_t st) {
-  int rc = ensure_pairs_smem_attr();
+// Stable pairs with payload word V.  64-bit payloads take no staged-load
+// fallback: their outputs must be 16-byte aligned (the C ABI checks).
+template <typename V>
+static int sort_pairs_typed(const uint32_t *kin, const V *vin, uint32_t *kout, V *vout, int64_t n,
+                            int dt, void *tmp, cudaStream_t st) {
+  constexpr bool V64 = sizeof(V) == 8;
+  int rc = ensure_pairs_smem_attr<V>();
   if (rc != NSORT_OK) return rc;
-  const Plan p = make_plan(NSORT_KIND_PAIRS, (uint64_t)n);
+  const Plan p = make_plan(V64 ? NSORT_KIND_PAIRS64 : NSORT_KIND_PAIRS, (uint64_t)n);
   char *t = static_cast<char *>(tmp);
   uint32_t *kb[2] = {kout, p.merge_passes ? reinterpret_cast<uint32_t *>(t + p.keys_off) : nullptr};
-  uint32_t *vb[2] = {vout, p.merge_passes ? reinterpret_cast<uint32_t *>(t + p.vals_off) : nullptr};
+  V *vb[2] = {vout, p.merge_passes ? reinterpret_cast<V *>(t + p.vals_off) : nullptr};
   int64_t *split = p.merge_passes ? reinterpret_cast<int64_t *>(t + p.split_off) : nullptr;
   int *status = p.merge_passes ? reinterpret_cast<int *>(t + p.status_off) : nullptr;
   uint32_t *samp = p.merge_passes ? reinterpret_cast<uint32_t *>(t + p.samp_off) : nullptr;
@@ -1405,17 +1459,18 @@ int sort_pairs_impl(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, ui
   const int64_t tiles = (n + p.sort_tile - 1) / p.sort_tile;
   {
     TraceScope tr(TK_TILE_SORT_PAIRS, st);
-    launch_tile_sort_pairs(kin, vin, kb[cur], vb[cur], n, dt, p.merge_passes == 0,
-                           (unsigned)tiles, tma ? samp : nullptr, st);
+    launch_tile_sort_pairs<V>(kin, vin, kb[cur], vb[cur], n, dt, p.merge_passes == 0,
+                              (unsigned)tiles, tma ? samp : nullptr, st);
   }
   rc = launch_status("tile_sort_pairs");
   for (int pass = 0; rc == NSORT_OK && pass < p.merge_passes; ++pass) {
     const int64_t run = (int64_t)p.sort_tile << pass;
     const int dt_out = pass == p.merge_passes - 1 ? dt : DT_U32;
     if (tma) {
-      launch_merge_tma(kb[cur], vb[cur], kb[cur ^ 1], vb[cur ^ 1], n, run, split, status, dt_out,
-                       samp, pass == p.merge_passes - 1 ? nullptr : samp, (pass & 1) == 0, st);
-    } else {
+      launch_merge_tma<V>(kb[cur], vb[cur], kb[cur ^ 1], vb[cur ^ 1], n, run, split, status,
+                          dt_out, samp, pass == p.merge_passes - 1 ? nullptr : samp,
+                          (pass & 1) == 0, st);
+    } else if constexpr (!V64) {
       {
         TraceScope tr(TK_PARTITION, st);
         launch_partition(kb[cur], n, run, p, PMERGE_TILE, split, st);
@@ -1423,11 +1478,24 @@ int sort_pairs_impl(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, ui
       TraceScope tr(TK_MERGE_PAIRS, st);
       launch_merge_pairs(kb[cur], vb[cur], kb[cur ^ 1], vb[cur ^ 1], n, run, split, dt_out,
                          (unsigned)p.num_merge_tiles, st);
+    } else {
+      set_last_error("nsort_pairs64: outputs must be 16-byte aligned");
+      return NSORT_EINVAL;
     }
     rc = launch_status("merge_pairs");
     cur ^= 1;
   }
   return rc;
+}
+
+int sort_pairs_impl(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
+                    int64_t n, int dt, void *tmp, cudaStream_t st) {
+  return sort_pairs_typed<uint32_t>(kin, vin, kout, vout, n, dt, tmp, st);
+}
+
+int sort_pairs64_impl(const uint32_t *kin, const uint64_t *vin, uint32_t *kout, uint64_t *vout,
+                      int64_t n, int dt, void *tmp, cudaStream_t st) {
+  return sort_pairs_typed<uint64_t>(kin, vin, kout, vout, n, dt, tmp, st);
 }
 
 // ---- merging sorted runs of any lengths (the local merge of a sharded sort)
@@ -1735,7 +1803,7 @@ static bool is_wide(int dtype) {
 
 extern "C" size_t nsort_temp_bytes(int kind, uint64_t n, uint64_t nseg, int dtype) {
   if (kind == NSORT_KIND_KEYS) return make_plan(kind, n, is_wide(dtype) ? dtype : 0).total;
-  if (kind == NSORT_KIND_PAIRS) return make_plan(kind, n).total;
+  if (kind == NSORT_KIND_PAIRS || kind == NSORT_KIND_PAIRS64) return make_plan(kind, n).total;
   if (kind == NSORT_KIND_MERGE) return merge_runs_temp_bytes(false, n, nseg, dtype);
   if (kind == NSORT_KIND_MERGE_PAIRS) return merge_runs_temp_bytes(true, n, nseg, dtype);
   return segmented_temp_bytes(kind, n, nseg);
@@ -1847,6 +1915,21 @@ extern "C" int nsort_merge_shards(const void *d_keys_in, const uint32_t *d_vals_
   }
   return merge_runs_impl(d_keys_in, d_vals_in, d_keys_out, d_vals_out, h_run_off, nruns, dtype,
                          d_tmp, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int nsort_pairs64(const void *d_keys_in, const uint64_t *d_vals_in, void *d_keys_out,
+                             uint64_t *d_vals_out, uint64_t n, int dtype, void *d_tmp,
+                             size_t tmp_bytes, void *stream) {
+  int rc = check_common(d_keys_in, d_keys_out, n, dtype, d_tmp, tmp_bytes, NSORT_KIND_PAIRS64);
+  if (rc != NSORT_OK || n == 0) return rc;
+  if (!d_vals_in || !d_vals_out) return NSORT_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(d_vals_in) | reinterpret_cast<uintptr_t>(d_vals_out)) & 7)
+    return NSORT_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(d_keys_out) | reinterpret_cast<uintptr_t>(d_vals_out)) & 15)
+    return NSORT_EINVAL;
+  return sort_pairs64_impl(static_cast<const uint32_t *>(d_keys_in), d_vals_in,
+                           static_cast<uint32_t *>(d_keys_out), d_vals_out, (int64_t)n, dtype,
+                           d_tmp, static_cast<cudaStream_t>(stream));
 }
 
 extern "C" const char *nsort_status_string(int status) {

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libnsort.so")
 U32, I32, F32 = 0, 1, 2
 U64, I64, F64 = 3, 4, 5           # 64-bit keys (nsort_keys only)
 KIND_KEYS, KIND_PAIRS, KIND_SEGMENTED, KIND_SEGMENTED_PAIRS = 0, 1, 2, 3
-KIND_MERGE, KIND_MERGE_PAIRS = 4, 5
+KIND_MERGE, KIND_MERGE_PAIRS, KIND_PAIRS64 = 4, 5, 6
 OK, EINVAL, ENOMEM, ECUDA, EBUSY, ETIMEOUT, ENOTFOUND = range(7)
 NET_BITONIC, NET_ODDEVEN, NET_BEST = 0, 1, 2     # include/nsort_ablation.h
 MERGE_HYBRID, MERGE_SHUFFLE, MERGE_SERIAL = 0, 1, 2
@@ -95,6 +95,8 @@ def _load():
         lib.nsort_keys.restype = i32
         lib.nsort_pairs.argtypes = [vp, vp, vp, vp, u64, i32, vp, sz, vp]
         lib.nsort_pairs.restype = i32
+        lib.nsort_pairs64.argtypes = [vp, vp, vp, vp, u64, i32, vp, sz, vp]
+        lib.nsort_pairs64.restype = i32
         lib.nsort_segmented.argtypes = [vp, vp, vp, vp, vp, u64, u64, i32, vp, sz, vp]
         lib.nsort_segmented.restype = i32
         lib.nsort_device_status.argtypes = [vp, vp]
@@ -226,6 +228,13 @@ def nsort_pairs(keys_in, vals_in, keys_out, vals_out, n: int, dtype: int, tmp, t
                 stream=None) -> int:
     return _load().nsort_pairs(_ptr(keys_in), _ptr(vals_in), _ptr(keys_out), _ptr(vals_out), n,
                                dtype, _ptr(tmp), tmp_bytes, _stream(stream))
+
+
+def nsort_pairs64(keys_in, vals_in, keys_out, vals_out, n: int, dtype: int, tmp, tmp_bytes: int,
+                  stream=None) -> int:
+    """nsort_pairs with 64-bit payloads (vals: 8-byte words)."""
+    return _load().nsort_pairs64(_ptr(keys_in), _ptr(vals_in), _ptr(keys_out), _ptr(vals_out), n,
+                                 dtype, _ptr(tmp), tmp_bytes, _stream(stream))
 
 
 def nsort_segmented(keys_in, keys_out, vals_in, vals_out, offsets, nseg: int, n: int,
