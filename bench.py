@@ -457,8 +457,8 @@ def time_sort(nsort, torch, fn, reps: int = 5, warm: int = 2):
 def bench_configs(nsort, torch):
     """The other plain-sort configurations: 2^28 int32 / float32 keys over
     the five distributions (uniform, sorted, reverse, 16 distinct, Zipf), 2^27 stable float32 key / uint32 value pairs
-    (Normal(0,1) with 0.1% IEEE specials, payload = index), and 2^27 64-bit
-    keys."""
+    (Normal(0,1) with 0.1% IEEE specials, payload = index), the same keys
+    with 64-bit payloads, and 2^27 64-bit keys."""
     from paper_2409_03970_gb300 import inputs
     n = 1 << 28
     out = {}
@@ -496,6 +496,17 @@ def bench_configs(nsort, torch):
     out["pairs_f32_normal_specials_2e27"] = {
         "ms": ms, "gpairs_s": m / ms / 1e6, "passes": passes,
         "hbm_roofline_frac": passes * 16 * m / (ms / 1e3) / 1e9 / load_peaks()["hbm_gbs"]}
+    del vt, vout, tmp
+    torch.cuda.empty_cache()
+    # the same keys with 64-bit payloads (nsort_pairs64): 24 B per pair per pass
+    vt = torch.arange(m, dtype=torch.int64, device="cuda")
+    vout = torch.empty_like(vt)
+    tmp = nsort.scratch(nsort.KIND_PAIRS64, m)
+    ms = time_sort(nsort, torch, lambda: nsort.nsort_pairs64(kt, vt, kout, vout, m, nsort.F32, tmp,
+                                                             tmp.numel()))
+    out["pairs64_f32_normal_specials_2e27"] = {
+        "ms": ms, "gpairs_s": m / ms / 1e6, "passes": passes,
+        "hbm_roofline_frac": passes * 24 * m / (ms / 1e3) / 1e9 / load_peaks()["hbm_gbs"]}
     del kt, vt, kout, vout, tmp
     torch.cuda.empty_cache()
     out.update(bench_keys64(nsort, torch))
