@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched (segmented) and served measurements")
-    ap.add_argument("--workload", choices=["plain", "segmented", "served", "ablation"],
+    ap.add_argument("--workload", choices=["plain", "segmented", "served", "ablation", "sharded"],
                     default="plain",
                     help="plain: the headline line (with batched/served extras); segmented / "
                          "served: that measurement alone, as its own line")
@@ -693,6 +693,72 @@ def bench_batched(nsort, torch, nseg: int, reps: int = 5):
             "candidates": len(tune["table"])}
 
 
+def bench_sharded(nsort, torch, nshards: int = 8, log2n: int = 28):
+    """The sharded sort's steps on one GPU: 2^28 uniform u32 keys cut into
+    `nshards` equal shards.  Device times (CUDA events) of what each GPU of
+    an nshards-GPU run does: sort its shard, find the segmentation points
+    (here one co-rank kernel over all shards), and merge its part's nshards
+    runs; plus the whole one-GPU emulation (every shard sorted, slices
+    gathered by device copies, every part merged), checked for order."""
+    from paper_2409_03970_gb300 import inputs, shard
+    n = 1 << log2n
+    x = torch.from_numpy(inputs.keys(n, "u32", "uniform", seed=0).view(np.int32)).cuda()
+    s = [(r * n) // nshards for r in range(nshards + 1)]
+    m = s[1] - s[0]
+    sk = torch.empty_like(x)
+    tmp = nsort.scratch(nsort.KIND_KEYS, max(s[r + 1] - s[r] for r in range(nshards)))
+    shard_ms = time_sort(nsort, torch, lambda: nsort.nsort_keys(x[:m], sk[:m], m, nsort.U32, tmp,
+                                                                 tmp.numel()))
+    for r in range(nshards):
+        a, b = s[r], s[r + 1]
+        rc = nsort.nsort_keys(x[a:b], sk[a:b], b - a, nsort.U32, tmp, tmp.numel())
+        assert rc == nsort.OK
+    del tmp
+    d = shard.part_bounds(n, nshards)
+    off_t = torch.tensor(s, dtype=torch.int64, device="cuda")
+    tgt_t = torch.tensor(d, dtype=torch.int64, device="cuda")
+    cr = torch.empty((nshards + 1) * nshards, dtype=torch.int64, device="cuda")
+    corank_ms = time_sort(nsort, torch, lambda: nsort.nsort_shard_coranks(
+        sk, off_t, nshards, tgt_t, nshards + 1, nsort.U32, cr), reps=21, warm=3)
+    c = cr.view(nshards + 1, nshards).cpu().numpy()
+    # the largest part: its slices gathered back to back, then merged
+    q = int(np.argmax(np.diff(d)))
+    lens = c[q + 1] - c[q]
+    run_off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    p = int(run_off[-1])
+    rk = torch.empty(p, dtype=torch.int32, device="cuda")
+    for r in range(nshards):
+        a, b = s[r] + int(c[q][r]), s[r] + int(c[q + 1][r])
+        rk[run_off[r]:run_off[r + 1]].copy_(sk[a:b])
+    ko = torch.empty_like(rk)
+    tmp = nsort.scratch(nsort.KIND_MERGE, p, nshards)
+    merge_ms = time_sort(nsort, torch, lambda: nsort.nsort_merge_shards(
+        rk, None, ko, None, run_off, nsort.U32, tmp, tmp.numel()))
+    passes = max(1, (nshards - 1).bit_length())      # a tree of pairwise passes
+    del rk, ko, tmp, sk
+    torch.cuda.empty_cache()
+    res = {}
+    whole_ms = time_sort(nsort, torch, lambda: res.update(
+        out=shard.sort_sharded_one_gpu(x, nshards, nsort.U32)[0]), reps=3, warm=1)
+    y = res.pop("out")
+    ordered = bool((y[1:].view(torch.int32).to(torch.int64) & 0xFFFFFFFF).ge(
+        y[:-1].view(torch.int32).to(torch.int64) & 0xFFFFFFFF).all())
+    del x, y
+    torch.cuda.empty_cache()
+    per_gpu = shard_ms + corank_ms + merge_ms
+    return {"workload": f"2^{log2n} uniform u32 keys as {nshards} shards of 2^{log2n}/{nshards}",
+            "shard_sort_ms": shard_ms, "corank_ms": corank_ms,
+            "part_merge_ms": merge_ms, "part_keys": p, "part_runs": nshards,
+            "part_merge_gkeys_s": p / merge_ms / 1e6,
+            "part_merge_passes": passes,
+            "part_merge_hbm_frac": passes * 8 * p / (merge_ms / 1e3) / 1e9 / load_peaks()["hbm_gbs"],
+            "per_gpu_compute_ms": per_gpu,
+            "one_gpu_emulation_ms": whole_ms, "one_gpu_emulation_ordered": ordered,
+            "note": "per_gpu_compute_ms = shard sort + co-ranks + part merge; an "
+                    f"{nshards}-GPU run adds the all-to-all exchange and the "
+                    "bisection's all-reduces"}
+
+
 def bench_served(nsort, torch, duration: float, rate: float = 2000.0, budget: int = 64 << 30,
                  streams: int = 8, batch_max_keys: int = 1 << 16, seed: int = 0):
     """Open-loop Poisson arrivals (rate/s for `duration` s), sizes log-uniform
@@ -840,6 +906,12 @@ def main():
                         "value": r["block_sort"]["table"]["best"][16], "unit": "GKeys/s",
                         "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
                         "dtype": "u32", "config": r, "vs_baseline": None}
+            elif args.workload == "sharded":
+                r = bench_sharded(nsort, torch)
+                line = {"metric": "sharded sort steps on one GPU: per-GPU compute ms of an 8-way split",
+                        "value": r["per_gpu_compute_ms"], "unit": "ms", "n_gpus": 1,
+                        "higher_is_better": False, "data": "synthetic", "dtype": "u32",
+                        "config": r, "vs_baseline": None}
             else:
                 r = bench_served(nsort, torch, args.served_duration)
                 line = {"metric": "served sort stream: keys/s and p50/p99 latency vs plain FIFO",
@@ -941,7 +1013,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.dtype)
 
-    batched = served = configs = None
+    batched = served = configs = sharded = None
     if rank == 0 and world == 1 and not args.no_extras:
         del x, out, tmp, host_in
         torch.cuda.empty_cache()
@@ -950,6 +1022,8 @@ def main():
         batched = bench_batched(nsort, torch, args.segments)
         torch.cuda.empty_cache()
         served = bench_served(nsort, torch, args.served_duration)
+        torch.cuda.empty_cache()
+        sharded = bench_sharded(nsort, torch)
         torch.cuda.empty_cache()
 
     if rank == 0:
@@ -977,6 +1051,7 @@ def main():
             "other_configs": configs,
             "batched": batched,
             "served": served,
+            "sharded_one_gpu": sharded,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
