@@ -39,6 +39,15 @@ int nsort_policy_arena_replay(uint64_t capacity, const int64_t *ops, int nops,
  * or faulting a GPU.  Paper: none. */
 int nsort_selftest_wait(void *d_tmp, size_t tmp_bytes, uint32_t limit_us, void *stream);
 
+/* Sets the smallest key count at which a sort of 32-bit keys merges two
+ * levels per pass over the array (four-way passes) and returns the previous
+ * setting.  0 selects four-way passes for every sort with at least two
+ * merge levels, UINT64_MAX for none.  Plans and nsort_temp_bytes follow the
+ * setting, so change it only while no sort runs, and size scratch after the
+ * change.  Makes no CUDA call.  Paper: none (a merge pass of this library
+ * merges one or two of the paper's merge levels). */
+uint64_t nsort_testing_set_four_way_min(uint64_t min_keys);
+
 #ifdef __cplusplus
 }
 #endif

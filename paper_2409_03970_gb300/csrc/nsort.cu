@@ -23,6 +23,7 @@
 #include <string>
 
 #include "nsort.h"
+#include "nsort_testing.h"
 #include "nsort_internal.h"
 #include "sort_device.cuh"
 #include "tma_device.cuh"
@@ -910,6 +911,420 @@ __global__ void __launch_bounds__(NT, PAIRS ? 3 : 4) merge_tma_kernel(
   if (tid == 0 && !ok) atomicExch(status, (int)NSORT_ETIMEOUT);
 }
 
+// ---- four-way merge passes ----------------------------------------------
+//
+// A four-way pass merges each group of four consecutive runs of `run` keys
+// into one run of 4 run keys with one read and one write of the array: the
+// two merge levels of the group (runs 0+1 and 2+3, then the two results)
+// run back to back on each tile, the first one in shared memory.  This
+// halves the passes over HBM of the merge phase.
+//
+// Tiles are cut at samples.  The pass's input samples (the key at every
+// SAMPLE-th position, written by the previous stage) of a group, merged in
+// stable (key, position) order, give every M4_M-th merged sample b as a tile
+// boundary.  Its co-rank c_r(b) in run r is the number of run-r keys that
+// precede it in the stable order of the group: keys <= key(b) for runs
+// before b's own run, keys < key(b) for runs after it, and b's own index in
+// its run.  If q_r samples of run r precede b, c_r(b) lies in
+// [SAMPLE q_r - SAMPLE + 1, SAMPLE q_r], so between two boundaries M4_M
+// samples apart the four runs give at most SAMPLE M4_M + 4 (SAMPLE - 1)
+// keys: a tile's size is bounded without an exact multiway selection.
+
+constexpr int M4_NT = 256;
+constexpr int M4_VT = 17;                 // outputs per thread, both levels
+constexpr int M4_M = 62;                  // merged samples per tile
+constexpr int M4_TMAX = SAMPLE * M4_M + 4 * (SAMPLE - 1);   // largest tile (4220)
+constexpr int M4_SENT = 24;               // largest keys behind each slice and level-one run
+constexpr int M4_IN_LEN = (M4_TMAX + 4 * (M4_SENT + 8) + 15) & ~15;   // one input buffer
+constexpr int M4_MID_LEN = (M4_TMAX + 2 * M4_SENT + 8 + 15) & ~15;    // level-one output
+constexpr int M4_WOUT = 32 * M4_VT;       // outputs per warp
+constexpr int M4_WSTRIDE = M4_WOUT + 4;   // per-warp staging, shifted to the 16-byte phase
+constexpr size_t M4_SMEM =
+    sizeof(uint32_t) * (2 * M4_IN_LEN + M4_MID_LEN + (M4_NT / 32) * M4_WSTRIDE);
+static_assert(M4_NT * M4_VT >= M4_TMAX, "level two covers the largest tile");
+static_assert((M4_TMAX + 2 * (M4_VT - 1)) / M4_VT <= M4_NT, "level one covers the largest tile");
+static_assert(M4_SENT >= M4_VT + 1, "the gap behind each run covers a merge's overrun");
+static_assert(M4_WOUT <= 32 * SAMPLE, "one sample per lane and warp slice");
+static_assert(M4_WOUT % 4 == 0, "warp output slices stay 16-byte multiples");
+constexpr int M4_CTAS = 3;                // resident CTAs per SM (shared memory bound)
+
+// The partition of a four-way pass runs in two kernels of CTAs that each take
+// SMG_CHUNK consecutive outputs of a merge of two sample runs: one warp finds
+// the chunk's first co-rank and another its last (32-ary searches), the CTA
+// stages both windows in shared memory and merges (or searches) there.
+constexpr int SMG_NT = 256;
+constexpr int SMG_CHUNK = 4096;
+constexpr int SMG_PER = SMG_CHUNK / SMG_NT;   // outputs per thread, level one
+constexpr int SMB_NT = 512;                   // level two: one warp per boundary at a time
+
+// Level one: the samples of runs 2p and 2p+1 (sample s is the key at
+// position SAMPLE s; rs samples per full run, ns in all) merged stably into
+// records (key << 32 | s), at the pair's own sample indices.  A chunk is
+// min(SMG_CHUNK, 2 rs) outputs, so no chunk crosses a pair.
+__global__ void __launch_bounds__(SMG_NT) sample_merge_kernel(const uint32_t *__restrict__ samp,
+                                                              int64_t ns, int64_t rs,
+                                                              uint64_t *__restrict__ rec) {
+  pdl_wait();
+  __shared__ uint32_t sk[SMG_CHUNK];   // the A window, then the B window
+  __shared__ int64_t cr[2];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t unit = 2 * rs;
+  const int64_t C = unit < SMG_CHUNK ? unit : SMG_CHUNK;
+  const int64_t c0 = (int64_t)blockIdx.x * C;
+  if (c0 >= ns) return;
+  const int64_t p0 = c0 - c0 % unit;
+  const int64_t la = ns - p0 < rs ? ns - p0 : rs;
+  const int64_t rest = ns - p0 - rs;
+  const int64_t lb = rest <= 0 ? 0 : (rest < rs ? rest : rs);
+  const uint32_t *A = samp + p0;
+  const uint32_t *B = A + la;
+  const int64_t d0 = c0 - p0;
+  const int64_t d1 = d0 + C < la + lb ? d0 + C : la + lb;
+  if (warp < 2)   // run 2p first on ties
+    cr[warp] = merge_path_global_group<32>(A, la, B, lb, warp ? d1 : d0, lane, 0xffffffffu);
+  __syncthreads();
+  const int64_t a0 = cr[0], b0 = d0 - a0;
+  const int na = (int)(cr[1] - a0), nb = (int)(d1 - cr[1] - b0);
+  for (int i = tid; i < na; i += SMG_NT) sk[i] = __ldg(A + a0 + i);
+  for (int i = tid; i < nb; i += SMG_NT) sk[na + i] = __ldg(B + b0 + i);
+  __syncthreads();
+  const int cnt = na + nb;
+  const int o = tid * SMG_PER;
+  if (o >= cnt) return;
+  int ia = merge_path_plain(sk, 0, na, na, nb, o);
+  int ib = o - ia;
+#pragma unroll 4
+  for (int k = 0; k < SMG_PER && o + k < cnt; ++k) {
+    const bool ta = ia < na && (ib >= nb || sk[ia] <= sk[na + ib]);
+    uint64_t r;
+    if (ta) {
+      r = ((uint64_t)sk[ia] << 32) | (uint64_t)(p0 + a0 + ia);
+      ++ia;
+    } else {
+      r = ((uint64_t)sk[na + ib] << 32) | (uint64_t)(p0 + la + b0 + ib);
+      ++ib;
+    }
+    rec[c0 + o + k] = r;
+  }
+}
+
+// Level two and the tile boundaries of a four-way pass.  Group g's records
+// are X (the level-one merge of runs 0 and 1) and then Y (runs 2 and 3); a
+// chunk is min(SMG_CHUNK, 4 rs) consecutive ranks of the merge of X and Y.
+// Interior boundary j of the group is the sample of merged rank j M4_M.  For
+// each one in its chunk a warp finds X's share x of the ranks below it (a
+// merge-path search of the staged windows), takes the boundary b = the
+// smaller of X[x] and Y[m - x], and reads from the first record of X and of
+// Y not before b how many samples of each run precede b (a record names its
+// run and its index there).  Then lanes 8r to 8r+7 count the keys of run r
+// before b among the at most SAMPLE - 1 keys where its co-rank can lie.
+// Writes c_r of every boundary record (tpg + 1 a group: the group's start,
+// its interior boundaries, and its end repeated up to tpg).
+__global__ void __launch_bounds__(SMB_NT) merge4_bounds_kernel(const uint32_t *__restrict__ src,
+                                                               const uint64_t *__restrict__ rec,
+                                                               int64_t n, int64_t run, int64_t tpg,
+                                                               int64_t *__restrict__ bnd) {
+  pdl_wait();
+  __shared__ uint64_t sr[SMG_CHUNK + 2];   // X window (+1 record), then Y window (+1)
+  __shared__ int64_t cr[2];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t unit = 4 * (run / SAMPLE);
+  const int64_t C = unit < SMG_CHUNK ? unit : SMG_CHUNK;
+  const int64_t c0 = (int64_t)blockIdx.x * C;
+  const int64_t g = c0 / unit;
+  const int64_t G0 = g * 4 * run;
+  auto len_of = [&](int q) {
+    const int64_t s = n - G0 - q * run;
+    return s <= 0 ? int64_t(0) : (s < run ? s : run);
+  };
+  auto samples_of = [&](int q) { return (len_of(q) + SAMPLE - 1) / SAMPLE; };
+  const int64_t nx = samples_of(0) + samples_of(1), ny = samples_of(2) + samples_of(3);
+  const int64_t cnt = nx + ny;
+  const int64_t tiles_g = (cnt + M4_M - 1) / M4_M;
+  const int64_t d0 = c0 - g * unit;
+  if (d0 >= cnt) return;   // past the samples of a partial last group
+  const int64_t d1 = d0 + C < cnt ? d0 + C : cnt;
+  int64_t *grec = bnd + 4 * g * (tpg + 1);
+  if (d0 == 0 && tid < 4) grec[tid] = 0;   // the group's start
+  if (d1 == cnt)                           // its end, in every record from tiles_g on
+    for (int64_t i = tiles_g * 4 + tid; i < (tpg + 1) * 4; i += SMB_NT) grec[i] = len_of((int)(i & 3));
+  const int64_t jf = d0 / M4_M + 1;        // interior boundaries with ranks in [d0, d1)
+  const int64_t jl = (d1 - 1) / M4_M;
+  if (jf > jl) return;
+  const uint64_t *X = rec + G0 / SAMPLE;
+  const uint64_t *Y = X + nx;
+  if (warp < 2)   // records are distinct
+    cr[warp] = merge_path_global_group<32>(X, nx, Y, ny, warp ? d1 : d0, lane, 0xffffffffu);
+  __syncthreads();
+  const int64_t a0 = cr[0], b0 = d0 - a0;
+  const int wa = (int)(cr[1] - a0), wb = (int)(d1 - cr[1] - b0);   // the chunk's windows
+  const int na = wa + (cr[1] < nx ? 1 : 0);                        // and one record more
+  const int nb = wb + (d1 - cr[1] < ny ? 1 : 0);
+  for (int i = tid; i < na; i += SMB_NT) sr[i] = __ldg(X + a0 + i);
+  for (int i = tid; i < nb; i += SMB_NT) sr[na + i] = __ldg(Y + b0 + i);
+  __syncthreads();
+  const int r = lane >> 3, sub = lane & 7;
+  const int64_t len_r = len_of(r);
+  const uint32_t *R = src + G0 + r * run;
+  for (int64_t j = jf + warp; j <= jl; j += SMB_NT / 32) {
+    const int64_t m = j * M4_M;
+    const int xl = merge_path_plain(sr, 0, wa, na, wb, (int)(m - d0));
+    const int64_t x = a0 + xl, y = m - x;
+    const bool hx = x < nx, hy = y < ny;
+    const uint64_t xr = hx ? sr[xl] : 0ull;
+    const uint64_t yr = hy ? sr[na + (int)(y - b0)] : 0ull;
+    const uint64_t bs = (hx && (!hy || xr < yr)) ? xr : yr;   // the boundary sample
+    const uint32_t vb = (uint32_t)(bs >> 32);
+    const int64_t ib = (int64_t)(uint32_t)bs * SAMPLE - G0;   // its position in the group
+    const int rb = (int)(ib / run);
+    int64_t c;
+    if (r == rb) {
+      c = ib - rb * run;
+    } else {
+      // samples of run r before b: from the first record of r's side not before b
+      const bool has = r < 2 ? hx : hy;
+      const uint64_t nr = r < 2 ? xr : yr;
+      const int64_t side = r < 2 ? x : y;
+      int64_t q = (len_r + SAMPLE - 1) / SAMPLE;
+      if (has) {
+        const int64_t pn = (int64_t)(uint32_t)nr * SAMPLE - G0;
+        const int rn = (int)(pn / run);
+        const int64_t in = (pn - rn * run) / SAMPLE;
+        q = rn == r ? in : side - in;
+      }
+      int64_t wlo = SAMPLE * q - (SAMPLE - 1);
+      int64_t whi = SAMPLE * q;
+      wlo = wlo > 0 ? wlo : 0;
+      whi = whi < len_r ? whi : len_r;
+      int before = 0;   // keys of the window before b (a prefix: the run is sorted)
+#pragma unroll
+      for (int i = 0; i < SAMPLE / 8; ++i) {
+        const int64_t k = wlo + sub + 8 * i;
+        if (k < whi) {
+          const uint32_t v = __ldg(R + k);
+          before += (r < rb ? v <= vb : v < vb) ? 1 : 0;
+        }
+      }
+      before += __shfl_xor_sync(0xffffffffu, before, 1);
+      before += __shfl_xor_sync(0xffffffffu, before, 2);
+      before += __shfl_xor_sync(0xffffffffu, before, 4);
+      c = wlo + before;
+    }
+    if (sub == 0) grec[4 * j + r] = c;
+  }
+}
+
+// A four-way tile: slice r of run r of its group starts at global index
+// off[r] and holds len[r] keys; in the input buffer its copy window starts
+// at base[r] (16-byte aligned) and its first key sits at sidx[r].
+struct Tile4 {
+  int64_t out0;
+  int64_t off[4];
+  int len[4];
+  int base[4];
+  int sidx[4];
+  int count;
+};
+
+// Tile u's geometry from its boundary co-ranks c[0..3] (its start) and
+// c[4..7] (its end).  A tile above M4_TMAX keys or with a negative slice
+// (neither occurs for sorted runs) is made empty and reported in *status.
+__device__ __forceinline__ Tile4 tile4_from(int64_t u, int64_t run, int64_t tpg,
+                                            const int64_t (&c)[8], int *status) {
+  Tile4 g;
+  const int64_t G0 = (u / tpg) * 4 * run;
+  int64_t out0 = G0, count = 0;
+  bool ok = true;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int64_t l = c[4 + r] - c[r];
+    ok = ok && l >= 0 && c[r] >= 0;
+    out0 += c[r];
+    count += l;
+  }
+  ok = ok && count <= M4_TMAX;
+  if (!ok) atomicCAS(status, 0, (int)NSORT_EINVAL);
+  g.out0 = out0;
+  g.count = ok ? (int)count : 0;
+  int base = 0;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    g.off[r] = G0 + r * run + c[r];
+    g.len[r] = ok ? (int)(c[4 + r] - c[r]) : 0;
+    g.base[r] = base;
+    g.sidx[r] = base + (int)(g.off[r] & 3);
+    base = (g.sidx[r] + g.len[r] + M4_SENT + 3) & ~3;
+  }
+  return g;
+}
+
+__device__ __forceinline__ void issue_tile4(const uint32_t *__restrict__ src, int64_t n_al,
+                                            const Tile4 &g, uint32_t *buf, uint64_t *bar) {
+  uint32_t bytes[4];
+  int64_t w0[4];
+  uint32_t total = 0;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    w0[r] = g.off[r] & ~int64_t(3);
+    int64_t w1 = (g.off[r] + g.len[r] + 3) & ~int64_t(3);
+    w1 = w1 < n_al ? w1 : n_al;
+    bytes[r] = (g.len[r] > 0 && w1 > w0[r]) ? (uint32_t)((w1 - w0[r]) * 4) : 0u;
+    total += bytes[r];
+  }
+  mbar_arrive_expect_tx(bar, total);
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+    if (bytes[r]) bulk_load(buf + g.base[r], src + w0[r], bytes[r], bar);
+}
+
+// The four-way pass.  Persistent CTAs, double-buffered bulk copies of each
+// tile's four slices as in merge_tma_kernel; per tile: level one (threads
+// split between the merges of slices 0+1 and 2+3 in proportion to their
+// sizes, M4_VT outputs each, into the shared level-one buffer), one CTA
+// barrier, level two (M4_VT outputs per thread), then per-warp staging and
+// bulk stores as in merge_tma_kernel.  Keys are order keys in; DT_OUT maps
+// them back on the last pass.  samp: the samples of the output (nullptr on
+// the last pass).
+template <int DT_OUT>
+__global__ void __launch_bounds__(M4_NT, M4_CTAS) merge4_tma_kernel(
+    const uint32_t *__restrict__ src, uint32_t *__restrict__ dst, int64_t n, int64_t run,
+    int64_t tpg, int64_t num_tiles, const int64_t *__restrict__ bnd, int *status, uint32_t *samp,
+    int reverse) {
+  pdl_wait();
+  extern __shared__ __align__(128) unsigned char m4_smem[];
+  uint32_t(*in_buf)[M4_IN_LEN] = reinterpret_cast<uint32_t(*)[M4_IN_LEN]>(m4_smem);
+  uint32_t *mid = reinterpret_cast<uint32_t *>(m4_smem) + 2 * M4_IN_LEN;
+  uint32_t *out_buf = mid + M4_MID_LEN;
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ Tile4 desc[2];
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
+  const int64_t n_al = n & ~int64_t(3);
+  const int64_t G = gridDim.x;
+  int64_t t = blockIdx.x;
+  auto tile_of = [&](int64_t i) { return reverse ? num_tiles - 1 - i : i; };
+  // boundary record of tile u: the group's records, then the tile's index in it
+  auto rec_of = [&](int64_t u) { return (u / tpg) * (tpg + 1) + (u % tpg); };
+  int64_t pf[8];   // thread 0: the co-ranks of loop index t + G
+  auto load_pf = [&](int64_t u) {
+    const int64_t *p = bnd + 4 * rec_of(u);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) pf[i] = __ldg(p + i);
+  };
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+    if (t < num_tiles) {
+      const int64_t u = tile_of(t);
+      load_pf(u);
+      desc[0] = tile4_from(u, run, tpg, pf, status);
+      issue_tile4(src, n_al, desc[0], in_buf[0], &bar[0]);
+    }
+    if (t + G < num_tiles) load_pf(tile_of(t + G));
+  }
+  __syncthreads();
+  bool ok = true;
+  uint32_t *wout = out_buf + warp * M4_WSTRIDE;
+  for (int it = 0; t < num_tiles; ++it, t += G) {
+    const int b = it & 1;
+    const int64_t tn = t + G;
+    const uint32_t parity = (uint32_t)((it >> 1) & 1);
+    const bool got = mbar_wait(&bar[b], parity);
+    if (!__syncthreads_and(got)) {
+      // a copy did not arrive in time: wait (bounded) for the copies still
+      // in flight into this CTA's shared memory, report, and stop
+      if (tid == 0) mbar_wait(&bar[b], parity);
+      ok = false;
+      break;
+    }
+    // every thread is past the previous tile: its buffer and descriptor are free
+    if (tid == 0 && tn < num_tiles) {
+      desc[b ^ 1] = tile4_from(tile_of(tn), run, tpg, pf, status);
+      issue_tile4(src, n_al, desc[b ^ 1], in_buf[b ^ 1], &bar[b ^ 1]);
+      if (tn + G < num_tiles) load_pf(tile_of(tn + G));
+    }
+    const Tile4 &g = desc[b];   // read in place: the merges index its slices at run time
+    uint32_t *s = in_buf[b];
+    // every warp: the keys past n_al that the copies left out, then the
+    // largest-key sentinels behind each slice (the same values in every warp)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      if (g.off[r] + g.len[r] > n_al && lane < 3) {
+        const int64_t i = (g.off[r] > n_al ? g.off[r] : n_al) + lane;
+        if (i < g.off[r] + g.len[r]) s[g.sidx[r] + (int)(i - g.off[r])] = __ldg(src + i);
+      }
+      for (int i = lane; i < M4_SENT; i += 32) s[g.sidx[r] + g.len[r] + i] = ~0u;
+    }
+    fence_proxy_async_smem();   // ordered before later bulk copies into this buffer
+    __syncwarp();
+    // level one: X = slices 0+1 into mid[0, lx), Y = slices 2+3 into mid[yb, yb + ly)
+    const int lx = g.len[0] + g.len[1], ly = g.len[2] + g.len[3];
+    const int yb = (lx + M4_SENT + 3) & ~3;
+    const int tx = (lx + M4_VT - 1) / M4_VT, ty = (ly + M4_VT - 1) / M4_VT;
+    uint32_t o[M4_VT];
+    if (tid < tx + ty) {
+      const bool onx = tid < tx;
+      const int p = onx ? 0 : 2;
+      const int diag = (onx ? tid : tid - tx) * M4_VT;
+      const int a0 = g.sidx[p], b0 = g.sidx[p + 1];
+      const int ai = merge_path_plain(s, a0, g.len[p], b0, g.len[p + 1], diag);
+      serial_merge_sentinel<M4_VT>(s, a0 + ai, b0 + diag - ai, o);
+      const int left = (onx ? lx : ly) - diag;
+      uint32_t *w = mid + (onx ? 0 : yb) + diag;
+#pragma unroll
+      for (int k = 0; k < M4_VT; ++k)
+        if (k < left) w[k] = o[k];
+    }
+    for (int i = tid; i < M4_SENT; i += M4_NT) {
+      mid[lx + i] = ~0u;
+      mid[yb + ly + i] = ~0u;
+    }
+    __syncthreads();
+    // level two: X and Y into this thread's M4_VT outputs
+    const int diag = tid * M4_VT < g.count ? tid * M4_VT : g.count;
+    const int ai = merge_path_plain(mid, 0, lx, yb, ly, diag);
+    serial_merge_sentinel<M4_VT>(mid, ai, yb + diag - ai, o);
+    // this warp's slice of the output: stage, then one bulk store
+    const int w0 = warp * M4_WOUT;
+    const int wcount = g.count - w0 < 0 ? 0 : (g.count - w0 < M4_WOUT ? g.count - w0 : M4_WOUT);
+    const int64_t gb = g.out0 + w0;
+    const int sh = (int)(gb & 3);
+    uint32_t *ws = wout + sh;
+    if (lane == 0) bulk_wait_read_all();   // the warp's previous stores have left its slice
+    __syncwarp();
+    if (g.count - w0 >= M4_WOUT) {
+#pragma unroll
+      for (int k = 0; k < M4_VT; ++k) ws[lane * M4_VT + k] = from_key(o[k], DT_OUT);
+    } else {
+#pragma unroll
+      for (int k = 0; k < M4_VT; ++k)
+        if (tid * M4_VT + k < g.count) ws[lane * M4_VT + k] = from_key(o[k], DT_OUT);
+    }
+    fence_proxy_async_smem();
+    __syncwarp();
+    if (samp && wcount > 0) {   // every SAMPLE-th output key, for the next pass
+      const int e = (int)((SAMPLE - (gb & (SAMPLE - 1))) & (SAMPLE - 1)) + SAMPLE * lane;
+      if (e < wcount) store_keep_in_l2(samp + (gb + e) / SAMPLE, ws[e]);
+    }
+    if (wcount > 0) {
+      const int hd = (4 - sh) & 3;
+      const int head = hd < wcount ? hd : wcount;
+      const int body = (wcount - head) & ~3;
+      const int tail = wcount - head - body;
+      if (lane == 0 && body) {
+        bulk_store(dst + gb + head, ws + head, (uint32_t)body * 4u);
+        bulk_commit();
+      }
+      if (lane < head) dst[gb + lane] = ws[lane];
+      if (lane < tail) dst[gb + head + body + lane] = ws[head + body + lane];
+    }
+  }
+  if (lane == 0) bulk_wait_all();
+  if (tid == 0 && !ok) atomicExch(status, (int)NSORT_ETIMEOUT);
+}
+
 // ------------------------------------------------------------- host side
 
 namespace {
@@ -979,6 +1394,45 @@ int64_t pair_tiles(int64_t n, int64_t run, int tile, int64_t *tpp_out) {
   return full * tpp + (rem + tile - 1) / tile;
 }
 
+// ---- four-way passes (host) ----------------------------------------------
+
+// Smallest sort (32-bit keys) whose merge phase takes four-way passes; below
+// it every pass is two-way.  Changed only by the test hook.
+static std::atomic<uint64_t> g_four_way_min{~uint64_t(0)};
+
+static bool use_four_way(int64_t n, int merge_passes) {
+  return merge_passes >= 2 && (uint64_t)n >= g_four_way_min.load();
+}
+
+// Tiles of a four-way pass over n keys in runs of `run`: tpg per full group
+// of four runs, and those of the last, partial group.
+static int64_t merge4_tiles(int64_t n, int64_t run, int64_t *tpg_out, int64_t *groups_out) {
+  const int64_t tpg = (4 * (run / SAMPLE) + M4_M - 1) / M4_M;
+  const int64_t full = n / (4 * run);
+  int64_t tiles = full * tpg;
+  const int64_t g0 = full * 4 * run;
+  if (g0 < n) {
+    int64_t cnt = 0;
+    for (int q = 0; q < 4; ++q) {
+      const int64_t s = n - g0 - q * run;
+      const int64_t len = s <= 0 ? 0 : (s < run ? s : run);
+      cnt += (len + SAMPLE - 1) / SAMPLE;
+    }
+    tiles += (cnt + M4_M - 1) / M4_M;
+  }
+  if (tpg_out) *tpg_out = tpg;
+  if (groups_out) *groups_out = (n + 4 * run - 1) / (4 * run);
+  return tiles;
+}
+
+// Boundary records of the four-way passes of a plan (the most any pass
+// needs: the first four-way pass has the shortest runs).
+static int64_t merge4_records(int64_t n, int64_t run0) {
+  int64_t tpg = 0, groups = 0;
+  merge4_tiles(n, run0, &tpg, &groups);
+  return groups * (tpg + 1);
+}
+
 Plan make_plan(int kind, uint64_t n, int dtype) {
   Plan p;
   const bool pairs = kind == NSORT_KIND_PAIRS || kind == NSORT_KIND_PAIRS64;
@@ -993,6 +1447,11 @@ Plan make_plan(int kind, uint64_t n, int dtype) {
   const int64_t runs = (p.n + p.sort_tile - 1) / p.sort_tile;
   p.merge_passes = 0;
   while ((int64_t(1) << p.merge_passes) < runs) ++p.merge_passes;
+  // 32-bit keys: two merge levels per pass over HBM on large arrays, and a
+  // two-way pass first when the number of levels is odd
+  const bool four = kind == NSORT_KIND_KEYS && !wide && use_four_way(p.n, p.merge_passes);
+  p.merge4_passes = four ? p.merge_passes / 2 : 0;
+  p.merge2_passes = p.merge_passes - 2 * p.merge4_passes;
   p.num_merge_tiles = (p.n + fallback_tile - 1) / fallback_tile;
   // splitters: enough for the power-of-two tiling and for the pair-aligned
   // tiling of every pass
@@ -1008,7 +1467,15 @@ Plan make_plan(int kind, uint64_t n, int dtype) {
   p.vals_off = p.keys_off + kb;
   p.split_off = pairs ? p.vals_off + vb : p.keys_off + kb;
   p.samp_off = p.split_off + align_up((size_t)(max_tiles + 1) * sizeof(int64_t), 256);
-  p.total = p.merge_passes == 0 ? 0 : p.samp_off + align_up((size_t)(n / SAMPLE + 2) * kw, 256);
+  p.rec_off = p.samp_off + align_up((size_t)(n / SAMPLE + 2) * kw, 256);
+  p.bnd_off = p.rec_off;
+  if (four) {
+    const int64_t run0 = (int64_t)p.sort_tile << p.merge2_passes;   // the first four-way pass's runs
+    p.bnd_off = p.rec_off + align_up((size_t)(n / SAMPLE + 2) * sizeof(uint64_t), 256);
+    p.total = p.bnd_off + align_up((size_t)merge4_records(p.n, run0) * 4 * sizeof(int64_t), 256);
+  } else {
+    p.total = p.merge_passes == 0 ? 0 : p.rec_off;
+  }
   return p;
 }
 
@@ -1283,6 +1750,65 @@ static void launch_merge_tma(const uint32_t *src, const V *vsrc, uint32_t *dst, 
 #undef NSORT_MT1
 }
 
+template <int DT>
+static void merge4_attr() {
+  cudaFuncSetAttribute(merge4_tma_kernel<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)M4_SMEM);
+  cudaFuncSetAttribute(merge4_tma_kernel<DT>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+}
+
+// SMs x resident CTAs of the four-way kernel, found once per device.
+static int merge4_grid(int64_t tiles) {
+  static std::atomic<int> cached[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int g = dev < 64 ? cached[dev].load() : 0;
+  if (g == 0) {
+    merge4_attr<DT_U32>();
+    merge4_attr<DT_I32>();
+    merge4_attr<DT_F32>();
+    int sms = 0, occ = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, merge4_tma_kernel<DT_U32>, M4_NT, M4_SMEM);
+    g = (sms > 0 ? sms : 1) * (occ > 0 ? occ : 1);
+    if (dev < 64) cached[dev].store(g);
+  }
+  return (int)(tiles < g ? tiles : g);
+}
+
+// One four-way pass: the level-one merge of the input samples, the tile
+// boundaries, then the merge.  samp holds the input's samples and receives
+// the output's (unless samp_out is null: the last pass).
+static void launch_merge4(const uint32_t *src, uint32_t *dst, int64_t n, int64_t run,
+                          const uint32_t *samp, uint64_t *rec, int64_t *bnd, int *status,
+                          int dt_out, uint32_t *samp_out, int reverse, cudaStream_t st) {
+  const int64_t ns = (n + SAMPLE - 1) / SAMPLE;
+  int64_t tpg = 0, groups = 0;
+  const int64_t tiles = merge4_tiles(n, run, &tpg, &groups);
+  const unsigned grid = (unsigned)merge4_grid(tiles);
+  const int64_t rs = run / SAMPLE;
+  {
+    TraceScope tr(TK_SAMPLE_MERGE, st);
+    const int64_t c1 = 2 * rs < SMG_CHUNK ? 2 * rs : SMG_CHUNK;
+    launch_pdl(sample_merge_kernel, (unsigned)((ns + c1 - 1) / c1), SMG_NT, 0, st, samp, ns, rs,
+               rec);
+  }
+  {
+    TraceScope tr(TK_MERGE4_BOUNDS, st);
+    const int64_t c2 = 4 * rs < SMG_CHUNK ? 4 * rs : SMG_CHUNK;
+    launch_pdl(merge4_bounds_kernel, (unsigned)(groups * (4 * rs / c2)), SMB_NT, 0, st, src,
+               (const uint64_t *)rec, n, run, tpg, bnd);
+  }
+  TraceScope tr(TK_MERGE4_KEYS, st);
+#define NSORT_M4(DT)                                                                         \
+  launch_pdl(merge4_tma_kernel<DT>, grid, M4_NT, M4_SMEM, st, src, dst, n, run, tpg, tiles, \
+             (const int64_t *)bnd, status, samp_out, reverse)
+  if (dt_out == DT_U32) NSORT_M4(DT_U32);
+  else if (dt_out == DT_I32) NSORT_M4(DT_I32);
+  else NSORT_M4(DT_F32);
+#undef NSORT_M4
+}
+
 // ---- 64-bit keys -------------------------------------------------------------
 
 static void launch_tile_sort_keys64(const uint64_t *in, uint64_t *out, int64_t n, int dt,
@@ -1402,7 +1928,12 @@ int sort_keys_impl(const uint32_t *in, uint32_t *out, int64_t n, int dt, void *t
   // the bulk-copy merge pass needs 16-byte aligned ping-pong buffers (the
   // scratch always is); otherwise the staged-load pass is used
   const bool tma = !(reinterpret_cast<uintptr_t>(out) & 15);
-  int cur = p.merge_passes % 2;  // the last pass must land in bufs[0] == out
+  // the plan's passes: two-way ones (one level each) first, then four-way
+  // ones (two levels each); the staged-load fallback merges one level a pass
+  const int n2 = tma ? p.merge2_passes : p.merge_passes;
+  const int n4 = tma ? p.merge4_passes : 0;
+  const int npass = n2 + n4;
+  int cur = npass % 2;  // the last pass must land in bufs[0] == out
   const int64_t tiles = (n + p.sort_tile - 1) / p.sort_tile;
   {
     TraceScope tr(TK_TILE_SORT_KEYS, st);
@@ -1411,15 +1942,26 @@ int sort_keys_impl(const uint32_t *in, uint32_t *out, int64_t n, int dt, void *t
                             tma ? samp : nullptr, st);
   }
   int rc = launch_status("tile_sort_keys");
-  for (int pass = 0; rc == NSORT_OK && pass < p.merge_passes; ++pass) {
-    const int64_t run = (int64_t)p.sort_tile << pass;
-    const int dt_out = pass == p.merge_passes - 1 ? dt : DT_U32;
+  int64_t run = p.sort_tile;
+  for (int pass = 0; rc == NSORT_OK && pass < npass; ++pass) {
+    const bool last = pass == npass - 1;
+    const int dt_out = last ? dt : DT_U32;
+    if (pass >= n2) {   // (passes alternate direction as below)
+      launch_merge4(bufs[cur], bufs[cur ^ 1], n, run, samp,
+                    reinterpret_cast<uint64_t *>(t + p.rec_off),
+                    reinterpret_cast<int64_t *>(t + p.bnd_off), status, dt_out,
+                    last ? nullptr : samp, (pass & 1) == 0, st);
+      rc = launch_status("merge4_keys");
+      run *= 4;
+      cur ^= 1;
+      continue;
+    }
     if (tma) {
       // the partition reads the samples of this pass's input before the
       // merge overwrites them with the samples of its output
       // the tile sort writes low to high; passes then alternate direction
       launch_merge_tma<uint32_t>(bufs[cur], nullptr, bufs[cur ^ 1], nullptr, n, run, split,
-                                 status, dt_out, samp, pass == p.merge_passes - 1 ? nullptr : samp,
+                                 status, dt_out, samp, last ? nullptr : samp,
                                  (pass & 1) == 0, st);
     } else {
       {
@@ -1431,6 +1973,7 @@ int sort_keys_impl(const uint32_t *in, uint32_t *out, int64_t n, int dt, void *t
                         (unsigned)p.num_merge_tiles, st);
     }
     rc = launch_status("merge_keys");
+    run *= 2;
     cur ^= 1;
   }
   return rc;
@@ -1815,10 +2358,14 @@ extern "C" int nsort_plan_dtype(int kind, uint64_t n, int dtype, int *passes, in
   if (n > MAX_KEYS) return NSORT_EINVAL;
   if (is_wide(dtype) && kind != NSORT_KIND_KEYS) return NSORT_EINVAL;
   const Plan p = make_plan(kind, n, is_wide(dtype) ? dtype : 0);
-  if (passes) *passes = 1 + p.merge_passes;
+  if (passes) *passes = 1 + p.merge2_passes + p.merge4_passes;
   if (sort_tile) *sort_tile = p.sort_tile;
   if (merge_tile) *merge_tile = p.merge_tile;
   return NSORT_OK;
+}
+
+extern "C" uint64_t nsort_testing_set_four_way_min(uint64_t min_keys) {
+  return g_four_way_min.exchange(min_keys);
 }
 
 extern "C" int nsort_merge_grid(int kind, int dtype) {

@@ -19,13 +19,17 @@ struct Plan {
   int64_t n = 0;
   int sort_tile = 0;         // keys per tile-sort CTA
   int merge_tile = 0;        // outputs per merge CTA
-  int merge_passes = 0;      // ceil(log2(ceil(n / sort_tile)))
+  int merge_passes = 0;      // merge levels: ceil(log2(ceil(n / sort_tile)))
+  int merge2_passes = 0;     // passes over HBM that merge one level (pairs of runs)
+  int merge4_passes = 0;     // passes that merge two levels (groups of four runs; 32-bit keys)
   int64_t num_merge_tiles = 0;
   size_t status_off = 0;     // device status word (NSORT_OK / NSORT_ETIMEOUT)
   size_t keys_off = 0;       // ping-pong key buffer
   size_t vals_off = 0;       // ping-pong value buffer (pairs)
   size_t split_off = 0;      // int64 merge-path splitters, one per merge tile
   size_t samp_off = 0;       // keys: every 64th key of the last stage's output
+  size_t rec_off = 0;        // four-way passes: level-one merged sample records (uint64)
+  size_t bnd_off = 0;        // four-way passes: tile boundary co-ranks (4 int64 a record)
   size_t total = 0;          // bytes of scratch (0 when one tile holds everything)
 };
 
@@ -78,7 +82,8 @@ int merge_runs_impl(const void *kin, const uint32_t *vin, void *kout, uint32_t *
 // Kernel ids of the tracer (order of its name table).
 enum TraceKernel {
   TK_TILE_SORT_KEYS = 0, TK_TILE_SORT_PAIRS, TK_PARTITION, TK_MERGE_KEYS, TK_MERGE_PAIRS,
-  TK_SEG_BIN, TK_SEG_SORT, TK_SEG_MERGE, TK_SEG_COPY, TK_TILE_SORT_KEYS64, TK_MERGE_KEYS64
+  TK_SEG_BIN, TK_SEG_SORT, TK_SEG_MERGE, TK_SEG_COPY, TK_TILE_SORT_KEYS64, TK_MERGE_KEYS64,
+  TK_SAMPLE_MERGE, TK_MERGE4_BOUNDS, TK_MERGE4_KEYS
 };
 
 // Brackets one kernel launch with CUDA events on its stream while tracing

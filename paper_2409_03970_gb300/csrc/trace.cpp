@@ -17,7 +17,8 @@ namespace {
 const char *const kKernelNames[] = {"tile_sort_keys", "tile_sort_pairs", "partition",
                                     "merge_keys",     "merge_pairs",     "segmented_bin",
                                     "segmented_sort", "segmented_merge", "segmented_copy",
-                                    "tile_sort_keys64", "merge_keys64"};
+                                    "tile_sort_keys64", "merge_keys64",
+                                    "sample_merge",   "merge4_bounds",   "merge4_keys"};
 constexpr int kNumKernels = sizeof(kKernelNames) / sizeof(kKernelNames[0]);
 
 struct Rec {

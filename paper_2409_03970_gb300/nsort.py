@@ -123,6 +123,8 @@ def _load():
         lib.nsort_policy_arena_replay.restype = i32
         lib.nsort_selftest_wait.argtypes = [vp, sz, ctypes.c_uint32, vp]
         lib.nsort_selftest_wait.restype = i32
+        lib.nsort_testing_set_four_way_min.argtypes = [u64]
+        lib.nsort_testing_set_four_way_min.restype = u64
         lib.nsort_keys_noalloc.argtypes = [vp, vp, u64, i32, vp]
         lib.nsort_keys_noalloc.restype = i32
         lib.nsort_keys_noalloc_status.argtypes = [vp]
@@ -365,6 +367,15 @@ def nsort_selftest_wait(tmp, limit_us: int = 20000, stream=None) -> int:
     """Runs the library's bounded waits on events that never happen (test hook)."""
     return _load().nsort_selftest_wait(_ptr(tmp), tmp.numel() if hasattr(tmp, "numel") else 512,
                                        limit_us, _stream(stream))
+
+
+def nsort_testing_set_four_way_min(min_keys: int) -> int:
+    """Smallest 32-bit key sort that merges two levels per pass (test hook);
+    returns the previous setting."""
+    return int(_load().nsort_testing_set_four_way_min(min_keys))
+
+
+FOUR_WAY_NEVER = (1 << 64) - 1
 
 
 def policy_pick_batch(queue, batch_max_keys, max_batch=4096, max_batch_keys=1 << 24):

@@ -43,16 +43,31 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_plan_pass_counts(lib):
-    passes, st, mt = nsort.nsort_plan(nsort.KIND_KEYS, 1 << 28)
-    assert st & (st - 1) == 0 and mt > 0          # run lengths double from a power of two
-    # one tile sort + ceil(log2(2^28 / tile)) merge passes
-    assert passes == 1 + (28 - st.bit_length() + 1)
-    assert nsort.nsort_plan(nsort.KIND_KEYS, 1)[0] == 1
-    assert nsort.nsort_plan(nsort.KIND_KEYS, st)[0] == 1
-    assert nsort.nsort_plan(nsort.KIND_KEYS, st + 1)[0] == 2
-    assert nsort.nsort_plan(nsort.KIND_KEYS, 3 * st)[0] == 3
-    p2, st2, _ = nsort.nsort_plan(nsort.KIND_PAIRS, 1 << 27)
-    assert p2 == 1 + (27 - st2.bit_length() + 1)
+    prev = nsort.nsort_testing_set_four_way_min(nsort.FOUR_WAY_NEVER)
+    try:
+        passes, st, mt = nsort.nsort_plan(nsort.KIND_KEYS, 1 << 28)
+        assert st & (st - 1) == 0 and mt > 0          # run lengths double from a power of two
+        # one tile sort + ceil(log2(2^28 / tile)) merge passes of one level
+        levels = 28 - st.bit_length() + 1
+        assert passes == 1 + levels
+        assert nsort.nsort_plan(nsort.KIND_KEYS, 1)[0] == 1
+        assert nsort.nsort_plan(nsort.KIND_KEYS, st)[0] == 1
+        assert nsort.nsort_plan(nsort.KIND_KEYS, st + 1)[0] == 2
+        assert nsort.nsort_plan(nsort.KIND_KEYS, 3 * st)[0] == 3
+        # four-way passes merge two levels each, after a one-level pass when
+        # the number of levels is odd
+        nsort.nsort_testing_set_four_way_min(0)
+        assert nsort.nsort_plan(nsort.KIND_KEYS, 1 << 28)[0] == 1 + levels % 2 + levels // 2
+        assert nsort.nsort_plan(nsort.KIND_KEYS, st + 1)[0] == 2      # one level
+        assert nsort.nsort_plan(nsort.KIND_KEYS, 3 * st)[0] == 2      # two levels: one pass
+        assert nsort.nsort_plan(nsort.KIND_KEYS, 5 * st)[0] == 3      # three: two passes
+        # pairs and 64-bit keys merge one level a pass
+        p2, st2, _ = nsort.nsort_plan(nsort.KIND_PAIRS, 1 << 27)
+        assert p2 == 1 + (27 - st2.bit_length() + 1)
+        p3, st3, _ = nsort.nsort_plan(nsort.KIND_KEYS, 1 << 27, nsort.U64)
+        assert p3 == 1 + (27 - st3.bit_length() + 1)
+    finally:
+        nsort.nsort_testing_set_four_way_min(prev)
 
 
 def test_temp_bytes(lib):
@@ -68,6 +83,28 @@ def test_temp_bytes(lib):
     _, pst, pmt = nsort.nsort_plan(nsort.KIND_PAIRS, n)
     assert 8 * n <= tp <= 8 * n + 8 * (n // pmt + n // (2 * pst) + 3) + 4 * (n // 64 + 2) + 1280
     assert nsort.nsort_temp_bytes(99, n) == 0
+
+
+def test_temp_bytes_four_way(lib):
+    # four-way passes add the level-one sample records (8 bytes per 64 keys)
+    # and the tile boundaries (4 x 8 bytes per tile of about 3968 keys, plus
+    # one record per group of four runs: at most one per 3641 keys)
+    n = 1 << 24
+    prev = nsort.nsort_testing_set_four_way_min(nsort.FOUR_WAY_NEVER)
+    try:
+        two = nsort.nsort_temp_bytes(nsort.KIND_KEYS, n)
+        nsort.nsort_testing_set_four_way_min(0)
+        four = nsort.nsort_temp_bytes(nsort.KIND_KEYS, n)
+        # pairs and 64-bit keys are unaffected
+        pairs = nsort.nsort_temp_bytes(nsort.KIND_PAIRS, n)
+        wide = nsort.nsort_temp_bytes(nsort.KIND_KEYS, n, 0, nsort.U64)
+        nsort.nsort_testing_set_four_way_min(nsort.FOUR_WAY_NEVER)
+        assert pairs == nsort.nsort_temp_bytes(nsort.KIND_PAIRS, n)
+        assert wide == nsort.nsort_temp_bytes(nsort.KIND_KEYS, n, 0, nsort.U64)
+    finally:
+        nsort.nsort_testing_set_four_way_min(prev)
+    extra = four - two
+    assert 8 * (n // 64) <= extra <= 8 * (n // 64 + 2) + 32 * (n // 3600 + 2) + 512
 
 
 def test_argument_validation_needs_no_gpu(lib):
