@@ -1048,7 +1048,8 @@ __global__ void __launch_bounds__(SMB_NT) merge4_bounds_kernel(const uint32_t *_
   if (d0 == 0 && tid < 4) grec[tid] = 0;   // the group's start
   if (d1 == cnt)                           // its end, in every record from tiles_g on
     for (int64_t i = tiles_g * 4 + tid; i < (tpg + 1) * 4; i += SMB_NT) grec[i] = len_of((int)(i & 3));
-  const int64_t jf = d0 / M4_M + 1;        // interior boundaries with ranks in [d0, d1)
+  // interior boundaries with ranks in [d0, d1) (a chunk can start on one)
+  const int64_t jf = d0 == 0 ? 1 : (d0 + M4_M - 1) / M4_M;
   const int64_t jl = (d1 - 1) / M4_M;
   if (jf > jl) return;
   const uint64_t *X = rec + G0 / SAMPLE;
@@ -1127,9 +1128,11 @@ struct Tile4 {
 };
 
 // Tile u's geometry from its boundary co-ranks c[0..3] (its start) and
-// c[4..7] (its end).  A tile above M4_TMAX keys or with a negative slice
-// (neither occurs for sorted runs) is made empty and reported in *status.
-__device__ __forceinline__ Tile4 tile4_from(int64_t u, int64_t run, int64_t tpg,
+// c[4..7] (its end).  A tile whose co-ranks leave their runs or go
+// backwards, or that holds more than M4_TMAX keys (none of which occurs for
+// sorted runs and complete boundary records), is made empty and reported in
+// *status, so that no copy or store leaves the array.
+__device__ __forceinline__ Tile4 tile4_from(int64_t u, int64_t n, int64_t run, int64_t tpg,
                                             const int64_t (&c)[8], int *status) {
   Tile4 g;
   const int64_t G0 = (u / tpg) * 4 * run;
@@ -1137,8 +1140,10 @@ __device__ __forceinline__ Tile4 tile4_from(int64_t u, int64_t run, int64_t tpg,
   bool ok = true;
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
+    const int64_t rest = n - G0 - r * run;
+    const int64_t len = rest <= 0 ? 0 : (rest < run ? rest : run);
     const int64_t l = c[4 + r] - c[r];
-    ok = ok && l >= 0 && c[r] >= 0;
+    ok = ok && l >= 0 && c[r] >= 0 && c[4 + r] <= len;
     out0 += c[r];
     count += l;
   }
@@ -1219,7 +1224,7 @@ __global__ void __launch_bounds__(M4_NT, M4_CTAS) merge4_tma_kernel(
     if (t < num_tiles) {
       const int64_t u = tile_of(t);
       load_pf(u);
-      desc[0] = tile4_from(u, run, tpg, pf, status);
+      desc[0] = tile4_from(u, n, run, tpg, pf, status);
       issue_tile4(src, n_al, desc[0], in_buf[0], &bar[0]);
     }
     if (t + G < num_tiles) load_pf(tile_of(t + G));
@@ -1241,7 +1246,7 @@ __global__ void __launch_bounds__(M4_NT, M4_CTAS) merge4_tma_kernel(
     }
     // every thread is past the previous tile: its buffer and descriptor are free
     if (tid == 0 && tn < num_tiles) {
-      desc[b ^ 1] = tile4_from(tile_of(tn), run, tpg, pf, status);
+      desc[b ^ 1] = tile4_from(tile_of(tn), n, run, tpg, pf, status);
       issue_tile4(src, n_al, desc[b ^ 1], in_buf[b ^ 1], &bar[b ^ 1]);
       if (tn + G < num_tiles) load_pf(tile_of(tn + G));
     }

@@ -54,10 +54,13 @@ def gpu_sort(ns, bits, dt, inplace=False, offset=0, trace=False):
 
 
 # merge levels 2 (one four-way pass), 3 (a two-way pass, then a four-way
-# one), 4, 5 and 6; groups of 1-4 runs; ragged runs and groups
+# one), 4, 5, 6 and 10; groups of 1-4 runs; ragged runs and groups.  At
+# 2^23 + 5 the last pass's group holds 131,073 samples: its partition
+# chunks (4096 merged samples each) start on a tile boundary (rank
+# 126,976 = 62 x 2048)
 SIZES = [2 * TILE + 1, 3 * TILE, 3 * TILE + 7, 4 * TILE, 4 * TILE + 5, 5 * TILE + 1,
          8 * TILE - 3, 9 * TILE + 63, 16 * TILE + 1, 100_003, 1 << 20, (1 << 20) + 12345,
-         5 * (1 << 20) - 3]
+         5 * (1 << 20) - 3, (1 << 23) + 5]
 
 
 @pytest.mark.parametrize("n", SIZES)
