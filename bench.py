@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--served-duration", type=float, default=60.0,
                     help="seconds of Poisson arrivals in the served measurement (60 = the stated workload)")
     ap.add_argument("--segments", type=int, default=100_000)
+    ap.add_argument("--merge-ways", type=int, choices=[2, 4], default=2,
+                    help="merge levels per pass over the array for 32-bit keys: 2 = one level "
+                         "(the library's default), 4 = two levels (four-way passes)")
     ap.add_argument("--no-numa-bind", action="store_true",
                     help="do not restrict the process to the GPU's NUMA node")
     return ap.parse_args()
@@ -554,6 +557,33 @@ def bench_keys64(nsort, torch):
 
 # ---- batched (segmented) and served measurements -----------------------------
 
+def bench_merge_ways(nsort, torch):
+    """Plain sorts of uniform u32 keys with one merge level per pass over
+    the array (two-way passes, the default) and with two (four-way passes):
+    ms per sort at 2^20 to 2^28."""
+    from paper_2409_03970_gb300 import inputs
+    res = {}
+    for log2n in (20, 22, 24, 26, 28):
+        n = 1 << log2n
+        x = torch.from_numpy(inputs.keys(n, "u32", "uniform", seed=0).view(np.int32)).cuda()
+        y = torch.empty_like(x)
+        row = {}
+        for ways, setting in ((2, nsort.FOUR_WAY_NEVER), (4, 0)):
+            prev = nsort.nsort_testing_set_four_way_min(setting)
+            try:
+                tmp = nsort.scratch(nsort.KIND_KEYS, n)
+                row[f"{ways}-way_ms"] = time_sort(
+                    nsort, torch, lambda: nsort.nsort_keys(x, y, n, nsort.U32, tmp, tmp.numel()),
+                    reps=11, warm=3)
+                del tmp
+            finally:
+                nsort.nsort_testing_set_four_way_min(prev)
+        res[f"2^{log2n}"] = row
+        del x, y
+        torch.cuda.empty_cache()
+    return {"unit": "ms per sort", "table": res}
+
+
 def bench_ablation(nsort, torch):
     """Column-network, keys-per-thread and merger ablation (Tables 1-3).
 
@@ -619,6 +649,7 @@ def bench_ablation(nsort, torch):
     del x, y
     out["mergers"] = {"n": n_reg, "unit": "GKeys/s", "l2": "resident (64 MiB in + out)",
                       "table": mt}
+    out["merge_ways"] = bench_merge_ways(nsort, torch)
     n_blk = 1 << 26
     blk = table(n_blk, lambda ipt: [512 * ipt], 11)
     out["block_sort"] = {"n": n_blk, "unit": "GKeys/s", "l2": "inputs (256 MiB) larger than L2",
@@ -921,6 +952,8 @@ def main():
             print(json.dumps(line), flush=True)
         return
 
+    if args.merge_ways == 4:
+        nsort.nsort_testing_set_four_way_min(0)
     n = 1 << args.log2n
     code = {"u32": nsort.U32, "i32": nsort.I32, "f32": nsort.F32,
             "u64": nsort.U64, "i64": nsort.I64, "f64": nsort.F64}[args.dtype]
@@ -933,7 +966,7 @@ def main():
     out = torch.empty_like(x)
     tmp = nsort.scratch(nsort.KIND_KEYS, n, dtype=code)
     passes, sort_tile, merge_tile = nsort.nsort_plan(nsort.KIND_KEYS, n, code)
-    mk_name = "merge_keys64" if wide else "merge_keys"
+    mk_name = "merge_keys64" if wide else ("merge4_keys" if args.merge_ways == 4 else "merge_keys")
     stream = torch.cuda.current_stream()
     sh = stream.cuda_stream
 
@@ -1040,6 +1073,7 @@ def main():
                               "inputs not larger than L2: a small-case run, not a bench value"),
                        "sort_hbm_roofline_frac": sort_frac,
                        "sort_algorithmic_bytes": alg_bytes_sort,
+                       "merge_levels_per_pass": 2 if args.merge_ways == 4 and not wide else 1,
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline,
             "cpu_baseline": cpu,

@@ -930,11 +930,13 @@ __global__ void __launch_bounds__(NT, PAIRS ? 3 : 4) merge_tma_kernel(
 // samples apart the four runs give at most SAMPLE M4_M + 4 (SAMPLE - 1)
 // keys: a tile's size is bounded without an exact multiway selection.
 
-constexpr int M4_NT = 256;
-constexpr int M4_VT = 17;                 // outputs per thread, both levels
-constexpr int M4_M = 62;                  // merged samples per tile
-constexpr int M4_TMAX = SAMPLE * M4_M + 4 * (SAMPLE - 1);   // largest tile (4220)
-constexpr int M4_SENT = 24;               // largest keys behind each slice and level-one run
+constexpr int M4_NT = 128;
+constexpr int M4_VT = 35;                 // level-two outputs per thread: two chains
+constexpr int M4_H = (M4_VT + 1) / 2;     // outputs of the first chain
+constexpr int M4_M = 64;                  // merged samples per tile
+constexpr int M4_TMAX = SAMPLE * M4_M + 4 * (SAMPLE - 1);   // largest tile (4348)
+constexpr int M4_C1 = ((M4_TMAX + M4_NT - 1) / M4_NT) | 1;  // most level-one outputs per chain
+constexpr int M4_SENT = 40;               // largest keys behind each slice and level-one run
 constexpr int M4_IN_LEN = (M4_TMAX + 4 * (M4_SENT + 8) + 15) & ~15;   // one input buffer
 constexpr int M4_MID_LEN = (M4_TMAX + 2 * M4_SENT + 8 + 15) & ~15;    // level-one output
 constexpr int M4_WOUT = 32 * M4_VT;       // outputs per warp
@@ -942,8 +944,8 @@ constexpr int M4_WSTRIDE = M4_WOUT + 4;   // per-warp staging, shifted to the 16
 constexpr size_t M4_SMEM =
     sizeof(uint32_t) * (2 * M4_IN_LEN + M4_MID_LEN + (M4_NT / 32) * M4_WSTRIDE);
 static_assert(M4_NT * M4_VT >= M4_TMAX, "level two covers the largest tile");
-static_assert((M4_TMAX + 2 * (M4_VT - 1)) / M4_VT <= M4_NT, "level one covers the largest tile");
-static_assert(M4_SENT >= M4_VT + 1, "the gap behind each run covers a merge's overrun");
+static_assert(M4_SENT >= M4_C1 + 1 && M4_SENT >= M4_H + 1,
+              "the gap behind each run covers a chain's overrun");
 static_assert(M4_WOUT <= 32 * SAMPLE, "one sample per lane and warp slice");
 static_assert(M4_WOUT % 4 == 0, "warp output slices stay 16-byte multiples");
 constexpr int M4_CTAS = 3;                // resident CTAs per SM (shared memory bound)
@@ -1028,11 +1030,12 @@ __global__ void __launch_bounds__(SMB_NT) merge4_bounds_kernel(const uint32_t *_
   __shared__ uint64_t sr[SMG_CHUNK + 2];   // X window (+1 record), then Y window (+1)
   __shared__ int64_t cr[2];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int lrun = 63 - __clzll((unsigned long long)run);   // run is a power of two
   const int64_t unit = 4 * (run / SAMPLE);
   const int64_t C = unit < SMG_CHUNK ? unit : SMG_CHUNK;
   const int64_t c0 = (int64_t)blockIdx.x * C;
-  const int64_t g = c0 / unit;
-  const int64_t G0 = g * 4 * run;
+  const int64_t g = c0 >> (lrun - 4);   // unit = run / 16
+  const int64_t G0 = g << (lrun + 2);
   auto len_of = [&](int q) {
     const int64_t s = n - G0 - q * run;
     return s <= 0 ? int64_t(0) : (s < run ? s : run);
@@ -1077,7 +1080,7 @@ __global__ void __launch_bounds__(SMB_NT) merge4_bounds_kernel(const uint32_t *_
     const uint64_t bs = (hx && (!hy || xr < yr)) ? xr : yr;   // the boundary sample
     const uint32_t vb = (uint32_t)(bs >> 32);
     const int64_t ib = (int64_t)(uint32_t)bs * SAMPLE - G0;   // its position in the group
-    const int rb = (int)(ib / run);
+    const int rb = (int)(ib >> lrun);
     int64_t c;
     if (r == rb) {
       c = ib - rb * run;
@@ -1089,8 +1092,8 @@ __global__ void __launch_bounds__(SMB_NT) merge4_bounds_kernel(const uint32_t *_
       int64_t q = (len_r + SAMPLE - 1) / SAMPLE;
       if (has) {
         const int64_t pn = (int64_t)(uint32_t)nr * SAMPLE - G0;
-        const int rn = (int)(pn / run);
-        const int64_t in = (pn - rn * run) / SAMPLE;
+        const int rn = (int)(pn >> lrun);
+        const int64_t in = (pn - ((int64_t)rn << lrun)) / SAMPLE;
         q = rn == r ? in : side - in;
       }
       int64_t wlo = SAMPLE * q - (SAMPLE - 1);
@@ -1113,6 +1116,57 @@ __global__ void __launch_bounds__(SMB_NT) merge4_bounds_kernel(const uint32_t *_
     }
     if (sub == 0) grec[4 * j + r] = c;
   }
+}
+
+// One serial merge in shared memory, advanced one output at a time (the
+// (lo, hi) formulation of serial_merge_sentinel: the run with the smaller
+// head, its head, and the other run's head).  Two of these per thread give
+// the scheduler two independent chains of loads.
+struct MergeChain {
+  uint32_t hlo, hhi;
+  int ilo, ihi;
+  __device__ __forceinline__ void init(const uint32_t *s, int a, int b) {
+    const uint32_t ka = s[a], kb = s[b];
+    const bool t0 = ka <= kb;
+    hlo = t0 ? ka : kb;
+    hhi = t0 ? kb : ka;
+    ilo = t0 ? a : b;
+    ihi = t0 ? b : a;
+  }
+  __device__ __forceinline__ void step(const uint32_t *s) {
+    const int i = ilo + 1;
+    const uint32_t kn = s[i];
+    const bool p = kn <= hhi;
+    hlo = p ? kn : hhi;
+    ilo = p ? i : ihi;
+    hhi = p ? hhi : kn;
+    ihi = p ? ihi : i;
+  }
+};
+
+// Two merge-path searches in shared memory at once: A's share of the first
+// d0 outputs of merging s[a0, a0 + na) with s[b0, b0 + nb) into r0, and of
+// the first d1 outputs of merging s[c0, c0 + nc) with s[e0, e0 + ne) into r1.
+// Branch-free, so that the two chains of loads overlap: a search that has
+// finished keeps probing its answer, whose two loads stay inside the buffer
+// (at most A's first element past its end, at least one element before B).
+__device__ __forceinline__ void merge_path_pair(const uint32_t *s, int a0, int na, int b0, int nb,
+                                                int d0, int c0, int nc, int e0, int ne, int d1,
+                                                int &r0, int &r1) {
+  int lo0 = d0 - nb > 0 ? d0 - nb : 0, hi0 = d0 < na ? d0 : na;
+  int lo1 = d1 - ne > 0 ? d1 - ne : 0, hi1 = d1 < nc ? d1 : nc;
+  while (lo0 < hi0 || lo1 < hi1) {
+    const int m0 = (lo0 + hi0) >> 1, m1 = (lo1 + hi1) >> 1;
+    const bool p0 = s[a0 + m0] <= s[b0 + d0 - 1 - m0];
+    const bool p1 = s[c0 + m1] <= s[e0 + d1 - 1 - m1];
+    const bool g0 = lo0 < hi0, g1 = lo1 < hi1;
+    lo0 = g0 && p0 ? m0 + 1 : lo0;
+    hi0 = g0 && !p0 ? m0 : hi0;
+    lo1 = g1 && p1 ? m1 + 1 : lo1;
+    hi1 = g1 && !p1 ? m1 : hi1;
+  }
+  r0 = lo0;
+  r1 = lo1;
 }
 
 // A four-way tile: slice r of run r of its group starts at global index
@@ -1264,33 +1318,61 @@ __global__ void __launch_bounds__(M4_NT, M4_CTAS) merge4_tma_kernel(
     }
     fence_proxy_async_smem();   // ordered before later bulk copies into this buffer
     __syncwarp();
-    // level one: X = slices 0+1 into mid[0, lx), Y = slices 2+3 into mid[yb, yb + ly)
+    // level one: X = slices 0+1 into mid[0, lx), Y = slices 2+3 into
+    // mid[yb, yb + ly); every thread takes cx outputs of X and cy of Y and
+    // runs the two merges side by side
     const int lx = g.len[0] + g.len[1], ly = g.len[2] + g.len[3];
     const int yb = (lx + M4_SENT + 3) & ~3;
-    const int tx = (lx + M4_VT - 1) / M4_VT, ty = (ly + M4_VT - 1) / M4_VT;
-    uint32_t o[M4_VT];
-    if (tid < tx + ty) {
-      const bool onx = tid < tx;
-      const int p = onx ? 0 : 2;
-      const int diag = (onx ? tid : tid - tx) * M4_VT;
-      const int a0 = g.sidx[p], b0 = g.sidx[p + 1];
-      const int ai = merge_path_plain(s, a0, g.len[p], b0, g.len[p + 1], diag);
-      serial_merge_sentinel<M4_VT>(s, a0 + ai, b0 + diag - ai, o);
-      const int left = (onx ? lx : ly) - diag;
-      uint32_t *w = mid + (onx ? 0 : yb) + diag;
+    {
+      // odd counts: the threads' start positions then fall in different banks
+      const int cx = ((lx + M4_NT - 1) / M4_NT) | 1, cy = ((ly + M4_NT - 1) / M4_NT) | 1;
+      const int dx = tid * cx < lx ? tid * cx : lx, dy = tid * cy < ly ? tid * cy : ly;
+      int ax, ay;
+      merge_path_pair(s, g.sidx[0], g.len[0], g.sidx[1], g.len[1], dx, g.sidx[2], g.len[2],
+                      g.sidx[3], g.len[3], dy, ax, ay);
+      MergeChain X, Y;
+      X.init(s, g.sidx[0] + ax, g.sidx[1] + dx - ax);
+      Y.init(s, g.sidx[2] + ay, g.sidx[3] + dy - ay);
+      const int ex = lx - dx, ey = ly - dy;   // outputs this thread may store
+      uint32_t *wx = mid + dx, *wy = mid + yb + dy;
+      const int cm = cx > cy ? cx : cy;
+      // both chains step every time (past its count a chain only walks into
+      // largest-key sentinels); only the stores are predicated
 #pragma unroll
-      for (int k = 0; k < M4_VT; ++k)
-        if (k < left) w[k] = o[k];
+      for (int k = 0; k < M4_C1; ++k) {
+        if (k >= cm) break;
+        if (k < cx && k < ex) wx[k] = X.hlo;
+        if (k < cy && k < ey) wy[k] = Y.hlo;
+        X.step(s);
+        Y.step(s);
+      }
     }
     for (int i = tid; i < M4_SENT; i += M4_NT) {
       mid[lx + i] = ~0u;
       mid[yb + ly + i] = ~0u;
     }
     __syncthreads();
-    // level two: X and Y into this thread's M4_VT outputs
-    const int diag = tid * M4_VT < g.count ? tid * M4_VT : g.count;
-    const int ai = merge_path_plain(mid, 0, lx, yb, ly, diag);
-    serial_merge_sentinel<M4_VT>(mid, ai, yb + diag - ai, o);
+    // level two: X and Y into this thread's M4_VT outputs, as two chains
+    // (outputs 0 .. M4_H - 1 and M4_H .. M4_VT - 1)
+    uint32_t o[M4_VT];
+    {
+      const int d0 = tid * M4_VT < g.count ? tid * M4_VT : g.count;
+      const int d1 = tid * M4_VT + M4_H < g.count ? tid * M4_VT + M4_H : g.count;
+      int a2, b2;
+      merge_path_pair(mid, 0, lx, yb, ly, d0, 0, lx, yb, ly, d1, a2, b2);
+      MergeChain A, B;
+      A.init(mid, a2, yb + d0 - a2);
+      B.init(mid, b2, yb + d1 - b2);
+#pragma unroll
+      for (int k = 0; k < M4_H; ++k) {
+        o[k] = A.hlo;
+        A.step(mid);
+        if (k < M4_VT - M4_H) {
+          o[M4_H + k] = B.hlo;
+          B.step(mid);
+        }
+      }
+    }
     // this warp's slice of the output: stage, then one bulk store
     const int w0 = warp * M4_WOUT;
     const int wcount = g.count - w0 < 0 ? 0 : (g.count - w0 < M4_WOUT ? g.count - w0 : M4_WOUT);
