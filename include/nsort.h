@@ -281,7 +281,9 @@ int nsort_keys_noalloc_status(void *stream);
  * memory budget.  Requests (device-resident inputs and outputs owned by the
  * caller) are admitted as soon as a stream slot and budget for their scratch
  * are free; small requests are co-batched into one segmented launch;
- * admitted requests overlap on the device.  Each result is bit-identical to
+ * admitted requests overlap on the device, except that requests of 2^22
+ * keys or more (each fills the GPU) run one at a time, and while one runs
+ * smaller requests are admitted ahead of the next.  Each result is bit-identical to
  * the plain call on the same input.  Paper: none — the serving layer is this
  * library's extension around the Sec. 2.1 sort. */
 typedef struct nsort_ctx nsort_ctx;

@@ -15,12 +15,16 @@ extern "C" {
 
 /* Runs the server's admission choice on a waiting queue of `count`
  * requests (arrival order; kind, dtype and size each): which tickets the
- * next free stream slot takes together.  Writes them to out (capacity
- * `count`) and their number to *out_count. */
+ * next free stream slot takes together.  large_min_keys / large_running:
+ * the server's size from which requests run one at a time (2^22 keys;
+ * UINT64_MAX for none) and whether one such request is running, in which
+ * case the first smaller request goes ahead of waiting large ones.  Writes
+ * the tickets to out (capacity `count`) and their number to *out_count
+ * (0 when nothing may start). */
 int nsort_policy_pick_batch(const uint64_t *tickets, const int *kinds, const int *dtypes,
                             const uint64_t *ns, int count, uint64_t batch_max_keys,
-                            int max_batch, uint64_t max_batch_keys, uint64_t *out,
-                            int *out_count);
+                            int max_batch, uint64_t max_batch_keys, uint64_t large_min_keys,
+                            int large_running, uint64_t *out, int *out_count);
 
 /* Replays allocations and releases on the server's scratch arena (first
  * fit, 256-byte granules, coalescing).  ops[i] > 0 allocates ops[i] bytes

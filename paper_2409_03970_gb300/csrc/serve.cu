@@ -4,7 +4,9 @@
 // device arena of mem_budget_bytes for scratch, and pinned host buffers for
 // batch descriptors.  Requests wait in a FIFO queue; whenever a slot is
 // free and the arena can hold the scratch of the request at the head, it is
-// admitted: large requests run alone as nsort_keys / nsort_pairs; small ones
+// admitted (while a request of LARGE_MIN_KEYS keys or more runs, the next
+// such request waits and the first smaller one is admitted ahead of it):
+// large requests run alone as nsort_keys / nsort_pairs; small ones
 // (n <= batch_max_keys) are co-batched with the other waiting small requests
 // of the same kind and dtype into one segmented sort (a gather kernel packs
 // their keys, nsort_segmented sorts every request as its own segment, a
@@ -37,6 +39,9 @@ namespace serve {
 
 constexpr size_t MAX_BATCH = 4096;                 // requests per co-batch
 constexpr uint64_t MAX_BATCH_KEYS = uint64_t(1) << 24;
+// Requests of at least this many keys run one at a time (their sorts'
+// persistent merge grids fill every SM); smaller ones may pass them.
+constexpr uint64_t LARGE_MIN_KEYS = uint64_t(1) << 22;
 
 struct BatchItem {
   const uint32_t *kin;
@@ -92,6 +97,7 @@ struct Job {
   std::atomic<int> finished{0};
   double t_finish = 0;
   int status = NSORT_OK;     // launch status, reported to every request of the job
+  bool large = false;        // a request of at least LARGE_MIN_KEYS keys
 };
 
 struct Slot {
@@ -162,6 +168,7 @@ void launch(Ctx *c, int s, std::vector<Pending> &picked, std::vector<std::pair<s
   job->slot = s;
   for (auto &p : picked) job->tickets.push_back(p.ticket);
   job->allocs = allocs;
+  job->large = picked.size() == 1 && picked[0].n >= LARGE_MIN_KEYS;
   const double t = now_s();
   for (auto &p : picked) c->reqs[p.ticket].t_admit = t;
   int rc = NSORT_OK;
@@ -280,12 +287,16 @@ void scheduler(Ctx *c) {
       c->queue.clear();
       if (c->jobs.empty()) break;
     }
-    // admission: FIFO; the head's batch must fit in the arena
+    // admission: FIFO, except that while a large request runs the next
+    // one waits and smaller requests go ahead; the batch must fit in the arena
     for (int s = 0; s < (int)c->slots.size() && !c->queue.empty(); ++s) {
       if (c->slots[s].busy) continue;
-      std::vector<size_t> pos =
-          pick_batch(c->queue, c->batch_max_keys, MAX_BATCH, MAX_BATCH_KEYS);
-      const Pending &head = c->queue.front();
+      bool large_running = false;
+      for (auto &j : c->jobs) large_running = large_running || (j->large && !j->finished.load());
+      std::vector<size_t> pos = pick_batch(c->queue, c->batch_max_keys, MAX_BATCH, MAX_BATCH_KEYS,
+                                           LARGE_MIN_KEYS, large_running);
+      if (pos.empty()) break;   // only large requests wait, and one runs
+      const Pending &head = c->queue[pos[0]];
       const bool batch = c->batch_max_keys > 0 && head.n <= c->batch_max_keys;
       size_t need;
       if (batch) {
@@ -468,12 +479,15 @@ extern "C" int nsort_wait(nsort_ctx *ctx, uint64_t ticket, uint32_t timeout_ms) 
 
 extern "C" int nsort_policy_pick_batch(const uint64_t *tickets, const int *kinds, const int *dtypes,
                                        const uint64_t *ns, int count, uint64_t batch_max_keys,
-                                       int max_batch, uint64_t max_batch_keys, uint64_t *out,
+                                       int max_batch, uint64_t max_batch_keys,
+                                       uint64_t large_min_keys, int large_running, uint64_t *out,
                                        int *out_count) {
   if (count < 0 || !out || !out_count || max_batch < 1) return NSORT_EINVAL;
   std::deque<serve::Pending> q;
   for (int i = 0; i < count; ++i) q.push_back({tickets[i], kinds[i], dtypes[i], ns[i]});
-  const std::vector<size_t> pos = serve::pick_batch(q, batch_max_keys, (size_t)max_batch, max_batch_keys);
+  const std::vector<size_t> pos = serve::pick_batch(q, batch_max_keys, (size_t)max_batch,
+                                                    max_batch_keys, large_min_keys,
+                                                    large_running != 0);
   const std::vector<serve::Pending> got = serve::take(q, pos);
   for (size_t i = 0; i < got.size(); ++i) out[i] = got[i].ticket;
   *out_count = (int)got.size();

@@ -84,22 +84,32 @@ struct Pending {
   uint64_t n;
 };
 
-// The admission decision for one free stream slot: FIFO.  If the head
-// request is small (n <= batch_max_keys), every waiting small request of
-// the same kind and dtype joins it, in arrival order, up to max_batch
+// The admission decision for one free stream slot.  The batch starts at the
+// first waiting request it may take: the queue's head, unless a large
+// request (n >= large_min) is already running, in which case large requests
+// wait and the first request below large_min goes ahead of them.  If that
+// request is small (n <= batch_max_keys), every later waiting small request
+// of the same kind and dtype joins it, in arrival order, up to max_batch
 // requests and max_batch_keys keys.  Returns the queue positions of the
-// requests to run together (empty when the queue is empty); the caller
+// requests to run together (empty when nothing may start); the caller
 // removes them with take() once it has found memory for them.  Larger
-// requests run alone.
+// requests run alone.  A large sort fills the GPU by itself (its persistent
+// merge grids take every SM), so two at once only share it and both finish
+// late; one at a time, the first finishes at its own speed.
 inline std::vector<size_t> pick_batch(const std::deque<Pending> &queue, uint64_t batch_max_keys,
-                                      size_t max_batch, uint64_t max_batch_keys) {
+                                      size_t max_batch, uint64_t max_batch_keys,
+                                      uint64_t large_min = ~uint64_t(0),
+                                      bool large_running = false) {
   std::vector<size_t> out;
-  if (queue.empty()) return out;
-  const Pending &head = queue.front();
-  out.push_back(0);
+  size_t h = 0;
+  if (large_running)
+    while (h < queue.size() && queue[h].n >= large_min) ++h;
+  if (h >= queue.size()) return out;
+  const Pending &head = queue[h];
+  out.push_back(h);
   if (batch_max_keys == 0 || head.n > batch_max_keys) return out;
   uint64_t keys = head.n;
-  for (size_t i = 1; i < queue.size() && out.size() < max_batch; ++i) {
+  for (size_t i = h + 1; i < queue.size() && out.size() < max_batch; ++i) {
     const Pending &q = queue[i];
     if (q.kind == head.kind && q.dtype == head.dtype && q.n <= batch_max_keys &&
         keys + q.n <= max_batch_keys) {

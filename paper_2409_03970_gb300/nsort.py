@@ -117,7 +117,8 @@ def _load():
         lib.nsort_wait.restype = i32
         u64p = ctypes.POINTER(u64)
         i64p = ctypes.POINTER(ctypes.c_int64)
-        lib.nsort_policy_pick_batch.argtypes = [u64p, ip, ip, u64p, i32, u64, i32, u64, u64p, ip]
+        lib.nsort_policy_pick_batch.argtypes = [u64p, ip, ip, u64p, i32, u64, i32, u64, u64, i32,
+                                                u64p, ip]
         lib.nsort_policy_pick_batch.restype = i32
         lib.nsort_policy_arena_replay.argtypes = [u64, i64p, i32, i64p]
         lib.nsort_policy_arena_replay.restype = i32
@@ -378,7 +379,11 @@ def nsort_testing_set_four_way_min(min_keys: int) -> int:
 FOUR_WAY_NEVER = (1 << 64) - 1
 
 
-def policy_pick_batch(queue, batch_max_keys, max_batch=4096, max_batch_keys=1 << 24):
+SERVE_LARGE_MIN_KEYS = 1 << 22   # the server runs requests this large one at a time
+
+
+def policy_pick_batch(queue, batch_max_keys, max_batch=4096, max_batch_keys=1 << 24,
+                      large_min_keys=(1 << 64) - 1, large_running=False):
     """The server's admission choice for a queue of (ticket, kind, dtype, n)."""
     m = len(queue)
     T = (ctypes.c_uint64 * max(m, 1))(*[q[0] for q in queue])
@@ -388,7 +393,8 @@ def policy_pick_batch(queue, batch_max_keys, max_batch=4096, max_batch_keys=1 <<
     out = (ctypes.c_uint64 * max(m, 1))()
     cnt = ctypes.c_int()
     rc = _load().nsort_policy_pick_batch(T, K, D, N, m, batch_max_keys, max_batch, max_batch_keys,
-                                         out, ctypes.byref(cnt))
+                                         large_min_keys, int(large_running), out,
+                                         ctypes.byref(cnt))
     if rc != OK:
         raise NsortError(rc, "nsort_policy_pick_batch")
     return [out[i] for i in range(cnt.value)]

@@ -118,16 +118,33 @@ def test_error_paths(ns):
 
 
 def test_admitted_requests_overlap_and_match_alone(ns):
-    """Continuous batching admits a request while others are on the GPU:
-    two large requests on different stream slots, submitted back to back,
-    are both admitted before either completes (their admit-to-done
-    intervals overlap), and each result equals the oracle's."""
-    n = 1 << 26
-    reqs = [("keys", "u32", inputs.keys(n, "u32", "uniform", seed=31), None),
-            ("keys", "f32", inputs.keys(n, "f32", "zipf", seed=32), None)]
-    budget = 2 * ns.nsort_temp_bytes(ns.KIND_KEYS, n) + (1 << 20)
+    """Continuous batching admits a request while others are on the GPU: a
+    large request and one just below the size from which requests run one
+    at a time, on different stream slots and submitted back to back, are
+    both admitted before either completes (their admit-to-done intervals
+    overlap), and each result equals the oracle's."""
+    big, small = 1 << 26, ns.SERVE_LARGE_MIN_KEYS - 1
+    reqs = [("keys", "u32", inputs.keys(big, "u32", "uniform", seed=31), None),
+            ("keys", "f32", inputs.keys(small, "f32", "zipf", seed=32), None)]
+    budget = ns.nsort_temp_bytes(ns.KIND_KEYS, big) + ns.nsort_temp_bytes(ns.KIND_KEYS, small) \
+        + (1 << 20)
     outs, tm = run_all(ns, reqs, streams=2, batch_max_keys=0, budget=budget)
     assert not any(t["batched"] for t in tm)
     assert max(t["t_admit"] for t in tm) < min(t["t_done"] for t in tm)
+    for (kind, dt, k, v), (ko, _) in zip(reqs, outs):
+        np.testing.assert_array_equal(ko, oracle.sort_keys(k, dt))
+
+
+def test_large_requests_run_one_at_a_time(ns):
+    """Requests of at least SERVE_LARGE_MIN_KEYS keys fill the GPU by
+    themselves: with two free slots and memory for both, the second is
+    admitted only after the first completes.  Results equal the oracle's."""
+    n = 1 << 23
+    reqs = [("keys", "u32", inputs.keys(n, "u32", "uniform", seed=33), None),
+            ("keys", "i32", inputs.keys(n, "i32", "dup16", seed=34), None)]
+    budget = 2 * ns.nsort_temp_bytes(ns.KIND_KEYS, n) + (1 << 20)
+    outs, tm = run_all(ns, reqs, streams=2, batch_max_keys=0, budget=budget)
+    first, second = sorted(tm, key=lambda t: t["t_admit"])
+    assert second["t_admit"] >= first["t_done"]
     for (kind, dt, k, v), (ko, _) in zip(reqs, outs):
         np.testing.assert_array_equal(ko, oracle.sort_keys(k, dt))

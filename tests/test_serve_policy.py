@@ -1,6 +1,7 @@
 """Host-side policy of the sort server, checked without a GPU: the FIFO
-admission with co-batching of small requests, and the first-fit scratch
-arena (nsort_policy_* hooks, no CUDA calls)."""
+admission with co-batching of small requests and large requests one at a
+time, and the first-fit scratch arena (nsort_policy_* hooks, no CUDA
+calls)."""
 import pytest
 
 from paper_2409_03970_gb300 import build as nbuild
@@ -35,6 +36,22 @@ def test_batch_limits_and_disabled_batching():
     assert nsort.policy_pick_batch(q, 1 << 16, max_batch_keys=3500) == [1, 2, 3]
     assert nsort.policy_pick_batch(q, 0) == [1]                    # batching off: plain FIFO
     assert nsort.policy_pick_batch([], 1 << 16) == []
+
+
+def test_large_requests_run_one_at_a_time():
+    L = nsort.SERVE_LARGE_MIN_KEYS
+    q = [(1, K, 0, L), (2, P, 0, 4 * L), (3, K, 0, L - 1), (4, K, 0, 100), (5, K, 0, 50)]
+    # no large request running: plain FIFO, the large head runs alone
+    assert nsort.policy_pick_batch(q, 1 << 16, large_min_keys=L) == [1]
+    # one running: the large ones wait and the first smaller request goes ahead
+    assert nsort.policy_pick_batch(q, 1 << 16, large_min_keys=L, large_running=True) == [3]
+    # a small one that goes ahead still collects its class behind it
+    assert nsort.policy_pick_batch(q[:2] + q[3:], 1 << 16, large_min_keys=L,
+                                   large_running=True) == [4, 5]
+    # only large requests wait: nothing may start
+    assert nsort.policy_pick_batch(q[:2], 1 << 16, large_min_keys=L, large_running=True) == []
+    # without a large-size limit the flag changes nothing
+    assert nsort.policy_pick_batch(q, 1 << 16, large_running=True) == [1]
 
 
 def test_arena_first_fit_coalescing_and_exhaustion():
