@@ -5,7 +5,9 @@
 // batch descriptors.  Requests wait in a FIFO queue; whenever a slot is
 // free and the arena can hold the scratch of the request at the head, it is
 // admitted (while a request of LARGE_MIN_KEYS keys or more runs, the next
-// such request waits and the first smaller one is admitted ahead of it):
+// such request waits and the first smaller one is admitted ahead of it; the
+// next large one is enqueued behind the running one on the GPU, through a
+// completion event, once no smaller request waits):
 // large requests run alone as nsort_keys / nsort_pairs; small ones
 // (n <= batch_max_keys) are co-batched with the other waiting small requests
 // of the same kind and dtype into one segmented sort (a gather kernel packs
@@ -98,6 +100,10 @@ struct Job {
   double t_finish = 0;
   int status = NSORT_OK;     // launch status, reported to every request of the job
   bool large = false;        // a request of at least LARGE_MIN_KEYS keys
+  cudaEvent_t done_ev = nullptr;   // large jobs: recorded after their work
+  ~Job() {
+    if (done_ev) cudaEventDestroy(done_ev);
+  }
 };
 
 struct Slot {
@@ -160,8 +166,10 @@ void finish_now(Ctx *c, uint64_t t, int status) {
 }
 
 // Launches one job on slot s (the caller holds c->mu).  On a launch error
-// the requests complete at once with that status.
-void launch(Ctx *c, int s, std::vector<Pending> &picked, std::vector<std::pair<size_t, size_t>> &allocs) {
+// the requests complete at once with that status.  after: the completion
+// event of a large job this one must follow on the GPU (or null).
+void launch(Ctx *c, int s, std::vector<Pending> &picked, std::vector<std::pair<size_t, size_t>> &allocs,
+            cudaEvent_t after = nullptr) {
   Slot &slot = c->slots[s];
   auto job = std::make_unique<Job>();
   job->ctx = c;
@@ -172,6 +180,7 @@ void launch(Ctx *c, int s, std::vector<Pending> &picked, std::vector<std::pair<s
   const double t = now_s();
   for (auto &p : picked) c->reqs[p.ticket].t_admit = t;
   int rc = NSORT_OK;
+  if (after && cudaStreamWaitEvent(slot.stream, after, 0) != cudaSuccess) rc = NSORT_ECUDA;
   if (picked.size() == 1 && c->reqs[picked[0].ticket].batched == 0) {
     const Req &q = c->reqs[picked[0].ticket];
     void *tmp = allocs.empty() ? nullptr : c->arena_base + allocs[0].first;
@@ -236,6 +245,11 @@ void launch(Ctx *c, int s, std::vector<Pending> &picked, std::vector<std::pair<s
       }
     }
   }
+  if (job->large && cudaEventCreateWithFlags(&job->done_ev, cudaEventDisableTiming) == cudaSuccess &&
+      cudaEventRecord(job->done_ev, slot.stream) != cudaSuccess) {
+    cudaEventDestroy(job->done_ev);
+    job->done_ev = nullptr;
+  }
   // the job completes through the stream even when a launch failed, so its
   // scratch is released only after everything enqueued so far has run
   job->status = rc;
@@ -291,11 +305,25 @@ void scheduler(Ctx *c) {
     // one waits and smaller requests go ahead; the batch must fit in the arena
     for (int s = 0; s < (int)c->slots.size() && !c->queue.empty(); ++s) {
       if (c->slots[s].busy) continue;
-      bool large_running = false;
-      for (auto &j : c->jobs) large_running = large_running || (j->large && !j->finished.load());
+      int large_live = 0;          // large jobs enqueued and not finished
+      Job *large_last = nullptr;   // the latest of them
+      for (auto &j : c->jobs)
+        if (j->large && !j->finished.load()) {
+          ++large_live;
+          large_last = j.get();
+        }
       std::vector<size_t> pos = pick_batch(c->queue, c->batch_max_keys, MAX_BATCH, MAX_BATCH_KEYS,
-                                           LARGE_MIN_KEYS, large_running);
-      if (pos.empty()) break;   // only large requests wait, and one runs
+                                           LARGE_MIN_KEYS, large_live > 0);
+      cudaEvent_t after = nullptr;
+      if (pos.empty()) {
+        // only large requests wait and one runs: enqueue the next one behind
+        // it on the GPU (its stream waits for the running job's completion
+        // event), so that it starts without a round trip through this thread;
+        // at most one waits so
+        if (large_live != 1 || !large_last->done_ev) break;
+        pos = pick_batch(c->queue, c->batch_max_keys, MAX_BATCH, MAX_BATCH_KEYS);
+        after = large_last->done_ev;
+      }
       const Pending &head = c->queue[pos[0]];
       const bool batch = c->batch_max_keys > 0 && head.n <= c->batch_max_keys;
       size_t need;
@@ -315,7 +343,7 @@ void scheduler(Ctx *c) {
       std::vector<Pending> picked = take(c->queue, pos);
       if (batch)
         for (auto &p : picked) c->reqs[p.ticket].batched = 1;
-      launch(c, s, picked, allocs);
+      launch(c, s, picked, allocs, after);
     }
     // sleep until a submission, a completion or destruction; the short
     // time-out covers a completion notified between the scan and the wait

@@ -137,14 +137,34 @@ def test_admitted_requests_overlap_and_match_alone(ns):
 
 def test_large_requests_run_one_at_a_time(ns):
     """Requests of at least SERVE_LARGE_MIN_KEYS keys fill the GPU by
-    themselves: with two free slots and memory for both, the second is
-    admitted only after the first completes.  Results equal the oracle's."""
+    themselves and run one at a time, in arrival order, even with free
+    slots and memory: the next one is enqueued behind the running one.  The
+    second request here reads the first one's output as its input, so it
+    returns the oracle's result only if it ran after the first completed;
+    a smaller request submitted last still runs beside them."""
     n = 1 << 23
-    reqs = [("keys", "u32", inputs.keys(n, "u32", "uniform", seed=33), None),
-            ("keys", "i32", inputs.keys(n, "i32", "dup16", seed=34), None)]
-    budget = 2 * ns.nsort_temp_bytes(ns.KIND_KEYS, n) + (1 << 20)
-    outs, tm = run_all(ns, reqs, streams=2, batch_max_keys=0, budget=budget)
-    first, second = sorted(tm, key=lambda t: t["t_admit"])
-    assert second["t_admit"] >= first["t_done"]
-    for (kind, dt, k, v), (ko, _) in zip(reqs, outs):
-        np.testing.assert_array_equal(ko, oracle.sort_keys(k, dt))
+    x = torch.from_numpy(inputs.keys(n, "u32", "uniform", seed=33).view(np.int32)).cuda()
+    y, z = torch.empty_like(x), torch.empty_like(x)
+    m = ns.SERVE_LARGE_MIN_KEYS // 4
+    small = inputs.keys(m, "f32", "dup16", seed=34)
+    s_in = torch.from_numpy(small.view(np.int32)).cuda()
+    s_out = torch.empty_like(s_in)
+    budget = 3 * ns.nsort_temp_bytes(ns.KIND_KEYS, n) + (1 << 20)
+    with ns.SortServer(0, budget, 4, 0) as srv:
+        torch.cuda.synchronize()
+        t1 = srv.submit(x, y, n=n, dtype=DT["u32"])
+        t2 = srv.submit(y, z, n=n, dtype=DT["u32"])
+        t3 = srv.submit(s_in, s_out, n=m, dtype=DT["f32"])
+        tms = []
+        for t in (t1, t2, t3):
+            assert srv.wait(t, 120000) == ns.OK
+            done, tm = srv.poll(t)
+            assert done and tm["status"] == ns.OK
+            tms.append(tm)
+    want = oracle.sort_keys(x.cpu().numpy().view(np.uint32), "u32")
+    np.testing.assert_array_equal(y.cpu().numpy().view(np.uint32), want)
+    np.testing.assert_array_equal(z.cpu().numpy().view(np.uint32), want)
+    np.testing.assert_array_equal(s_out.cpu().numpy().view(np.uint32), oracle.sort_keys(small, "f32"))
+    assert tms[0]["t_done"] <= tms[1]["t_done"]
+    # the smaller request was admitted before the second large one completed
+    assert tms[2]["t_admit"] < tms[1]["t_done"]
