@@ -363,35 +363,37 @@ def copy_bandwidths(torch, host, dev_a, dev_b, reps: int = 3):
 def bench_e2e(nsort, torch, host_in, x, out, tmp, n, code, steps, world, esize=4):
     """The same sort through the public API with HOST buffers: every step
     copies its input from pinned host memory, sorts, and copies the result
-    back to pinned host memory.  Pipelined over three streams with double
-    buffers, so the upload of step i+1 and the download of step i-1 overlap
-    the sort of step i (the way a stream of host arrays is sorted); the
-    unpipelined time of one step is reported beside it."""
+    back to pinned host memory.  Pipelined over three streams with three
+    device arrays per direction, so the upload of step i+1 and the download
+    of step i-1 overlap the sort of step i (the way a stream of host arrays
+    is sorted) and neither copy waits on the other's buffer; the unpipelined
+    time of one step is reported beside it."""
     ke = max(3, min(steps, 50))     # fill and drain of the pipeline amortised over the steps
+    NB = 3                          # device buffers per direction
     h2d, comp, d2h = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
-    din = [x, torch.empty_like(x)]
-    dout = [out, torch.empty_like(out)]
-    hout = [torch.empty_like(host_in).pin_memory(), torch.empty_like(host_in).pin_memory()]
+    din = [x] + [torch.empty_like(x) for _ in range(NB - 1)]
+    dout = [out] + [torch.empty_like(out) for _ in range(NB - 1)]
+    hout = [torch.empty_like(host_in).pin_memory() for _ in range(NB)]
     ev = lambda: torch.cuda.Event(enable_timing=False)
-    up, sorted_, down = [ev(), ev()], [ev(), ev()], [ev(), ev()]
+    up, sorted_, down = [ev() for _ in range(NB)], [ev() for _ in range(NB)], [ev() for _ in range(NB)]
     tev = lambda: torch.cuda.Event(enable_timing=True)
     # per-step timing events, read after the loop: upload, sort, download
-    marks = [[tev() for _ in range(6)] for _ in range(2 + ke)]
+    marks = [[tev() for _ in range(6)] for _ in range(NB + ke)]
     torch.cuda.synchronize()
 
     def step(i):
-        b = i & 1
+        b = i % NB
         m = marks[i]
-        if i >= 2:
-            h2d.wait_event(sorted_[b])        # din[b] no longer read by step i-2
+        if i >= NB:
+            h2d.wait_event(sorted_[b])        # din[b] no longer read by step i-NB
         with torch.cuda.stream(h2d):
             m[0].record(h2d)
             din[b].copy_(host_in, non_blocking=True)
             m[1].record(h2d)
             up[b].record(h2d)
         comp.wait_event(up[b])
-        if i >= 2:
-            comp.wait_event(down[b])          # dout[b] downloaded by step i-2
+        if i >= NB:
+            comp.wait_event(down[b])          # dout[b] downloaded by step i-NB
         m[2].record(comp)
         rc = nsort.nsort_keys(din[b], dout[b], n, code, tmp, tmp.numel(), comp.cuda_stream)
         if rc != nsort.OK:
@@ -405,21 +407,21 @@ def bench_e2e(nsort, torch, host_in, x, out, tmp, n, code, steps, world, esize=4
             m[5].record(d2h)
             down[b].record(d2h)
 
-    for i in range(2):
+    for i in range(NB):
         step(i)
     torch.cuda.synchronize()
     barrier(world)
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(h2d)
-    for i in range(2, 2 + ke):
+    for i in range(NB, NB + ke):
         step(i)
     t1.record(d2h)
     torch.cuda.synchronize()
     barrier(world)
     ems, e2e_value = replica_throughput(t0.elapsed_time(t1) / ke, n, world)
     stages = {name: float(np.mean([marks[i][2 * j].elapsed_time(marks[i][2 * j + 1])
-                                   for i in range(2, 2 + ke)]))
+                                   for i in range(NB, NB + ke)]))
               for j, name in enumerate(("upload_ms", "sort_ms", "download_ms"))}
     # one step alone, start to finish (no overlap between steps); the best
     # of three, as for the copy bandwidths
@@ -438,7 +440,7 @@ def bench_e2e(nsort, torch, host_in, x, out, tmp, n, code, steps, world, esize=4
     return {"value": e2e_value, "unit": UNIT, "copy_bandwidths": bw,
             "stages_in_pipeline": stages,
             "h2d_bytes_per_step": esize * n, "d2h_bytes_per_step": esize * n, "ms_per_step": ems,
-            "steps": ke, "pipelined": "3 streams, double-buffered device arrays",
+            "steps": ke, "pipelined": f"3 streams, {NB} device arrays per direction",
             "one_step_unpipelined_ms": serial_ms}
 
 
