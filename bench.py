@@ -23,6 +23,7 @@ import glob
 import hashlib
 import json
 import os
+import re
 import subprocess
 import sys
 import tempfile
@@ -182,9 +183,15 @@ def load_peaks():
 
 
 def source_hash(files):
+    """Hash of the code in `files` with comments and blank lines left out:
+    an edit to a comment leaves the kernels, and so their traffic, as they
+    were; any other edit changes the hash."""
     h = hashlib.sha256()
     for f in files:
-        h.update(open(os.path.join(ROOT, f), "rb").read())
+        text = open(os.path.join(ROOT, f), encoding="utf-8").read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        h.update("\n".join(l.rstrip() for l in text.splitlines() if l.strip()).encode())
     return h.hexdigest()[:16]
 
 

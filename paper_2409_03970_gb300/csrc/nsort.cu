@@ -1237,13 +1237,13 @@ __device__ __forceinline__ void issue_tile4(const uint32_t *__restrict__ src, in
 }
 
 // The four-way pass.  Persistent CTAs, double-buffered bulk copies of each
-// tile's four slices as in merge_tma_kernel; per tile: level one (threads
-// split between the merges of slices 0+1 and 2+3 in proportion to their
-// sizes, M4_VT outputs each, into the shared level-one buffer), one CTA
-// barrier, level two (M4_VT outputs per thread), then per-warp staging and
-// bulk stores as in merge_tma_kernel.  Keys are order keys in; DT_OUT maps
-// them back on the last pass.  samp: the samples of the output (nullptr on
-// the last pass).
+// tile's four slices as in merge_tma_kernel; per tile: level one (every
+// thread merges an odd number of outputs of slices 0+1 and as many of
+// slices 2+3, as two interleaved chains, into the shared level-one
+// buffer), one CTA barrier, level two (M4_VT outputs per thread as two
+// interleaved chains), then per-warp staging and bulk stores as in
+// merge_tma_kernel.  Keys are order keys in; DT_OUT maps them back on the
+// last pass.  samp: the samples of the output (nullptr on the last pass).
 template <int DT_OUT>
 __global__ void __launch_bounds__(M4_NT, M4_CTAS) merge4_tma_kernel(
     const uint32_t *__restrict__ src, uint32_t *__restrict__ dst, int64_t n, int64_t run,

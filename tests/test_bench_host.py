@@ -51,7 +51,7 @@ def test_committed_traffic_is_plausible(bench):
 
 def test_traffic_goes_null_when_a_source_changes(bench, tmp_path, monkeypatch):
     src = tmp_path / "kernel.cu"
-    src.write_text("// version 1\n")
+    src.write_text("int a = 1;  // version 1\n/* the kernel */\n")
     (tmp_path / "profiles").mkdir()
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     entry = {"captured_n": 1 << 28, "read_bytes": 1 << 30, "write_bytes": 1 << 30,
@@ -59,5 +59,9 @@ def test_traffic_goes_null_when_a_source_changes(bench, tmp_path, monkeypatch):
     (tmp_path / "profiles" / "traffic.json").write_text(json.dumps({"merge_keys": entry}))
     assert bench.load_traffic("merge_keys")["read_bytes"] == 1 << 30
     assert bench.load_traffic("merge_pairs") is None
-    src.write_text("// version 2\n")
+    # a comment edit leaves the code, and the counters, as they were
+    src.write_text("int a = 1;  // version 2\n\n/* the kernel,\n   commented */\n")
+    assert bench.load_traffic("merge_keys")["read_bytes"] == 1 << 30
+    # a code edit does not
+    src.write_text("int a = 2;  // version 2\n")
     assert bench.load_traffic("merge_keys") is None
