@@ -100,3 +100,16 @@ def test_pairs64_rejects_misaligned_buffers(ns):
     assert ns.nsort_pairs64(k[:n], v[:n], k[2:n + 2], v[1:n + 1], n, 0, tmp,
                             tmp.numel()) == ns.EINVAL
     assert ns.nsort_pairs64(k[:n], v[:n], k[:n], v[:n], n, 0, tmp, tmp.numel() - 1) == ns.ENOMEM
+
+
+def test_full_size_pairs64_against_oracle(ns):
+    """The benchmark's 64-bit payload workload: 2^27 float32 Normal(0,1)
+    keys with 0.1% IEEE specials and payloads 0, 1, 2, ... as 64-bit words,
+    compared element by element (keys and payloads)."""
+    n = 1 << 27
+    k, _ = inputs.normal_pairs(n, seed=0)
+    v = np.arange(n, dtype=np.uint64)
+    gk, gv = gpu_pairs64(ns, k, v, "f32")
+    wk, wv = expected(k, v, "f32")
+    np.testing.assert_array_equal(gk, wk)
+    np.testing.assert_array_equal(gv, wv)

@@ -113,11 +113,13 @@ def test_keys64_scratch_too_small_is_rejected(ns):
     assert rc == ns.ENOMEM
 
 
-def test_full_size_u64_uniform_against_oracle(ns):
-    """2^27 uniform uint64 keys (1 GiB), in the launch configuration the
-    benchmark times, compared element by element."""
+@pytest.mark.parametrize("dt,dist", [("u64", "uniform"), ("i64", "uniform"), ("f64", "uniform"),
+                                     ("f64", "specials")])
+def test_full_size_keys64_against_oracle(ns, dt, dist):
+    """The benchmark's 64-bit key workloads: 2^27 keys (1 GiB) of each
+    dtype, on the benchmark's own inputs and launch configuration, compared
+    element by element."""
     n = 1 << 27
-    x = inputs.keys64(n, "u64", "uniform", seed=0)
-    got = gpu_sort64(ns, x, "u64")
-    want = oracle.sort_keys64(x, "u64")
-    assert np.array_equal(got, want)
+    x = inputs.keys64(n, dt, dist, seed=0)
+    got = gpu_sort64(ns, x, dt)
+    assert np.array_equal(got, oracle.sort_keys64(x, dt))
