@@ -177,6 +177,50 @@ __device__ __forceinline__ void warp_merge_level(K (&r)[IPT], int lane) {
   thread_tail<IPT>(r);
 }
 
+// Transposes a warp's 32 x 32 block of keys through t (32 rows of 33: the
+// padding keeps both the row writes and the column reads free of bank
+// conflicts): lane l's r[k] becomes lane k's r[l].  Its own inverse.
+template <typename K>
+__device__ __forceinline__ void warp_transpose32(K (&r)[32], K *t, int lane) {
+  __syncwarp();   // every lane is done reading t
+#pragma unroll
+  for (int k = 0; k < 32; ++k) t[lane * 33 + k] = r[k];
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < 32; ++k) r[k] = t[k * 33 + lane];
+}
+
+// warp_merge_level for 32 keys per thread with the cross-lane half-cleaners
+// done in-thread: after the flip stage (across lanes, by shuffles) the warp
+// transposes its block, so that element 32 l + k sits in lane k, register
+// l; a half-cleaner at lane distance d (lane l against lane l ^ d, the
+// lower lane keeping the minimum) is then a compare-exchange of registers
+// l and l ^ d in every lane.  A second transpose restores the lane-major
+// runs for the in-thread tail.  Per key: J - 1 shuffle stages (two
+// instructions on the integer pipe each, the lane decides min or max)
+// become J - 1 in-thread stages (one each) for four shared-memory accesses.
+template <int J, typename K>
+__device__ __forceinline__ void warp_merge_level_t(K (&r)[32], int lane, K *t) {
+  constexpr int span = 1 << J;
+  const bool lower = !(lane & (span >> 1));
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const K from_hi = shfl_x(r[31 - k], span - 1);
+    const K from_lo = shfl_x(r[k], span - 1);
+    r[k] = keep(lower, r[k], from_hi);
+    r[31 - k] = keep(lower, r[31 - k], from_lo);
+  }
+  warp_transpose32(r, t, lane);
+#pragma unroll
+  for (int d = span >> 2; d >= 1; d >>= 1) {
+#pragma unroll
+    for (int l = 0; l < 32; ++l)
+      if (!(l & d)) ce(r[l], r[l + d]);
+  }
+  warp_transpose32(r, t, lane);
+  thread_tail<32>(r);
+}
+
 // The five levels merge the warp's 32 runs into one sorted run of 32*IPT.
 // With levels < 5 only the first levels levels run: the warp then holds
 // sorted runs of IPT * 2^levels.
@@ -471,8 +515,21 @@ __device__ __forceinline__ void sort_tile_in_block(K (&r)[IPT], K *s) {
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   COLS::sort(r);
-  warp_merge<IPT>(r, lane);
-  if (TILE == 32 * IPT) return;
+  if constexpr (IPT == 32 && sizeof(K) == 4) {
+    // levels 3-5 transpose through this warp's part of s (32 x 33 keys)
+    static_assert(NT * 33 <= block_smem_len<K>(NT, IPT), "transpose buffers fit in s");
+    K *t = s + (tid >> 5) * (32 * 33);
+    warp_merge_level<1>(r, lane);
+    warp_merge_level<2>(r, lane);
+    warp_merge_level_t<3>(r, lane, t);
+    warp_merge_level_t<4>(r, lane, t);
+    warp_merge_level_t<5>(r, lane, t);
+    if (TILE == 32 * IPT) return;
+    __syncthreads();   // every warp is done with its transpose buffer
+  } else {
+    warp_merge<IPT>(r, lane);
+    if (TILE == 32 * IPT) return;
+  }
   const int e0 = tid * IPT;
   if (GAPPED) {
     stage_gapped(r, s, e0, 32 * IPT);
