@@ -190,29 +190,41 @@ __device__ __forceinline__ void warp_transpose32(K (&r)[32], K *t, int lane) {
   for (int k = 0; k < 32; ++k) r[k] = t[k * 33 + lane];
 }
 
-// warp_merge_level for 32 keys per thread with the cross-lane half-cleaners
-// done in-thread: after the flip stage (across lanes, by shuffles) the warp
-// transposes its block, so that element 32 l + k sits in lane k, register
-// l; a half-cleaner at lane distance d (lane l against lane l ^ d, the
-// lower lane keeping the minimum) is then a compare-exchange of registers
-// l and l ^ d in every lane.  A second transpose restores the lane-major
-// runs for the in-thread tail.  Per key: J - 1 shuffle stages (two
-// instructions on the integer pipe each, the lane decides min or max)
-// become J - 1 in-thread stages (one each) for four shared-memory accesses.
+// warp_merge_level for 32 keys per thread done on the transposed block:
+// after the transpose, element 32 l + k of the warp sits in lane k,
+// register l, so a group of 2^J lanes (the run pair this level merges) is
+// the 2^J registers [g 2^J, (g+1) 2^J) of every lane.  Instead of the flip
+// stage the second run of each pair is reversed (register l and its mirror
+// within that half swap between lanes k and 31 - k, one shuffle for every
+// two keys), which makes each pair a bitonic sequence; the J half-cleaner
+// stages (lane distances 2^(J-1) .. 1 before the transpose) are then
+// in-thread compare-exchanges of registers l and l + d, the lower keeping
+// the minimum.  A second transpose restores the lane-major runs for the
+// in-thread tail (distances 16 .. 1).  Per key and level: J shuffle stages
+// (a shuffle and two integer instructions each: the lane decides min or
+// max) become half a shuffle and J in-thread stages (one instruction each),
+// for four shared-memory accesses.
 template <int J, typename K>
 __device__ __forceinline__ void warp_merge_level_t(K (&r)[32], int lane, K *t) {
-  constexpr int span = 1 << J;
-  const bool lower = !(lane & (span >> 1));
-#pragma unroll
-  for (int k = 0; k < 16; ++k) {
-    const K from_hi = shfl_x(r[31 - k], span - 1);
-    const K from_lo = shfl_x(r[k], span - 1);
-    r[k] = keep(lower, r[k], from_hi);
-    r[31 - k] = keep(lower, r[31 - k], from_lo);
-  }
+  constexpr int G = 1 << J;    // registers per run pair after the transpose
+  constexpr int H = G >> 1;
   warp_transpose32(r, t, lane);
+  // reverse the second run of every pair: its registers l and m, mirrors
+  // within that half, each take the other's key from lane 31 - lane
+  static_assert(H % 2 == 0, "mirror registers pair up");
 #pragma unroll
-  for (int d = span >> 2; d >= 1; d >>= 1) {
+  for (int g = 0; g < 32 / G; ++g) {
+#pragma unroll
+    for (int i = 0; i < H / 2; ++i) {
+      const int l = g * G + H + i, m = g * G + G - 1 - i;
+      const K to_l = shfl_x(r[m], 31);
+      const K to_m = shfl_x(r[l], 31);
+      r[l] = to_l;
+      r[m] = to_m;
+    }
+  }
+#pragma unroll
+  for (int d = H; d >= 1; d >>= 1) {
 #pragma unroll
     for (int l = 0; l < 32; ++l)
       if (!(l & d)) ce(r[l], r[l + d]);
