@@ -233,6 +233,79 @@ __device__ __forceinline__ void warp_merge_level_t(K (&r)[32], int lane, K *t) {
   thread_tail<32>(r);
 }
 
+// The same for 16 keys per thread (64-bit words: the pairs' composites and
+// 64-bit keys), within each half-warp: lane 16h + l's r[k] becomes lane
+// 16h + k's r[l], through 256 words of t per half-warp.  An XOR swizzle
+// (row l, column k at 16 l + (k ^ l)) instead of padding keeps the row
+// writes and the column reads free of bank conflicts in the same space.
+template <typename K>
+__device__ __forceinline__ void halfwarp_transpose16(K (&r)[16], K *t, int lane) {
+  K *b = t + (lane >> 4) * 256;
+  const int l = lane & 15;
+  __syncwarp();   // every lane is done reading t
+#pragma unroll
+  for (int k = 0; k < 16; ++k) b[16 * l + (k ^ l)] = r[k];
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < 16; ++k) r[k] = b[16 * k + (l ^ k)];
+}
+
+// warp_merge_level_t for 16 keys per thread, levels 2-4 (run pairs within
+// a half-warp): after the half-warp transpose a run pair is 2^J registers
+// of the half-warp's 16 lanes; the second run is reversed (mirror
+// registers swap between lanes k and 15 - k) and every half-cleaner is
+// in-thread, then the transpose back and the in-thread tail.
+template <int J, typename K>
+__device__ __forceinline__ void warp_merge_level16_t(K (&r)[16], int lane, K *t) {
+  constexpr int G = 1 << J;
+  constexpr int H = G >> 1;
+  static_assert(J >= 2 && J <= 4, "run pairs within a half-warp");
+  halfwarp_transpose16(r, t, lane);
+#pragma unroll
+  for (int g = 0; g < 16 / G; ++g) {
+#pragma unroll
+    for (int i = 0; i < H / 2; ++i) {
+      const int l = g * G + H + i, m = g * G + G - 1 - i;
+      const K to_l = shfl_x(r[m], 15);
+      const K to_m = shfl_x(r[l], 15);
+      r[l] = to_l;
+      r[m] = to_m;
+    }
+  }
+#pragma unroll
+  for (int d = H; d >= 1; d >>= 1) {
+#pragma unroll
+    for (int l = 0; l < 16; ++l)
+      if (!(l & d)) ce(r[l], r[l + d]);
+  }
+  halfwarp_transpose16(r, t, lane);
+  thread_tail<16>(r);
+}
+
+// Level 5 for 16 keys per thread: the flip stage across the two half-warps
+// by shuffles, then the half-cleaners at lane distances 8 .. 1 in-thread on
+// the half-warp transposes, then the in-thread tail.
+template <typename K>
+__device__ __forceinline__ void warp_merge_level16_5t(K (&r)[16], int lane, K *t) {
+  const bool lower = !(lane & 16);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const K from_hi = shfl_x(r[15 - k], 31);
+    const K from_lo = shfl_x(r[k], 31);
+    r[k] = keep(lower, r[k], from_hi);
+    r[15 - k] = keep(lower, r[15 - k], from_lo);
+  }
+  halfwarp_transpose16(r, t, lane);
+#pragma unroll
+  for (int d = 8; d >= 1; d >>= 1) {
+#pragma unroll
+    for (int l = 0; l < 16; ++l)
+      if (!(l & d)) ce(r[l], r[l + d]);
+  }
+  halfwarp_transpose16(r, t, lane);
+  thread_tail<16>(r);
+}
+
 // The five levels merge the warp's 32 runs into one sorted run of 32*IPT.
 // With levels < 5 only the first levels levels run: the warp then holds
 // sorted runs of IPT * 2^levels.
@@ -536,6 +609,17 @@ __device__ __forceinline__ void sort_tile_in_block(K (&r)[IPT], K *s) {
     warp_merge_level_t<3>(r, lane, t);
     warp_merge_level_t<4>(r, lane, t);
     warp_merge_level_t<5>(r, lane, t);
+    if (TILE == 32 * IPT) return;
+    __syncthreads();   // every warp is done with its transpose buffer
+  } else if constexpr (IPT == 16 && sizeof(K) == 8 && GAPPED) {
+    // 64-bit keys: levels 2-5 use the half-warp transposes, 512 words of s
+    // per warp (the pairs' tile sort, at 64 registers, would spill)
+    K *t = s + (tid >> 5) * 512;
+    warp_merge_level<1>(r, lane);
+    warp_merge_level16_t<2>(r, lane, t);
+    warp_merge_level16_t<3>(r, lane, t);
+    warp_merge_level16_t<4>(r, lane, t);
+    warp_merge_level16_5t(r, lane, t);
     if (TILE == 32 * IPT) return;
     __syncthreads();   // every warp is done with its transpose buffer
   } else {
